@@ -1,0 +1,306 @@
+"""Benchmark of the GB300 TTM product (one JSON line on rank 0).
+
+Workload (the metric's configuration): two random right-canonical tensor trains,
+L = 30 sites, d = 2, bond chi = 512 with bond spectra shaped like 1/k, float64
+cores; TTM with eps = 1e-14 and chi_max = chi_out = 512. One step = one full
+product (all N contractions, N(N-1)/2 swaps, all QR gauge moves) through the
+C ABI. Inputs are resident in HBM for `value`; `e2e` repeats the step from
+pinned host buffers with the copies inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--chi X]
+
+Under torchrun (N > 1) every rank runs its own product (independent inputs, no
+collective on the data path: weak scaling); rank 0 prints the line.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TTM products/s + TFLOP/s at chi=512,d=2,L=30; mixed vs FP64 at rel err<=1e-7"
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz = 1.259
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--chi", type=int, default=512)
+    p.add_argument("--L", type=int, default=30)
+    p.add_argument("--eps", type=float, default=1e-14)
+    p.add_argument("--prec", default="fp64")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=1)
+    return p.parse_args()
+
+
+def workload(L, chi, seed):
+    import ttgen
+    A = ttgen.rand_tt_spectral(L, 2, chi, seed)
+    B = ttgen.rand_tt_spectral(L, 2, chi, seed + 1)
+    return A, B
+
+
+def config(args):
+    return {"workload": "config3: random right-canonical TT pair, L=%d, d=2, chi=%d, sigma_k ~ 1/k, "
+                        "float64 cores, eps=%g, chi_max=chi_out=%d" % (args.L, args.chi, args.eps, args.chi),
+            "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
+            "precision_mode": args.prec,
+            "l2": "flushed between timed steps (256 MiB write outside the timed events)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, flops_per_product, swap_flops_full, n_samples=2):
+    """The oracle's Swap (numpy/LAPACK float64) on full-size carriages, extrapolated to one
+    product by counted flops. Returns (products/s, seconds spent, description)."""
+    from oracle import ttm as ottm
+    rng = np.random.default_rng(7)
+    chi = args.chi
+    X = np.linalg.qr(rng.standard_normal((2 * chi, chi)))[0].reshape(chi, 2, chi)
+    Y = rng.standard_normal((chi, 2, chi)) / chi
+    t0 = time.perf_counter()
+    for _ in range(n_samples):
+        ottm.swap(X, Y, args.eps, chi)
+    dt = (time.perf_counter() - t0) / n_samples
+    per_product = dt * flops_per_product / swap_flops_full
+    return 1.0 / per_product, dt * n_samples, (
+        "%d full-size oracle Swaps (%dx2x%d carriages, numpy/LAPACK gesdd, %d host threads), "
+        "%.2f s each, extrapolated to one product by counted flops (%.3g / %.3g)"
+        % (n_samples, chi, chi, os.cpu_count(), dt, flops_per_product, swap_flops_full))
+
+
+def swap_model_flops(chi):
+    m = n = 2 * chi
+    return 2.0 * 4 * chi ** 3 + 2.0 * m * n * n + 2.0 * m * n * chi
+
+
+def model_flops(L, d, chi):
+    """Counted flops of one product from the schedule of Sec. II.B with every bond at its
+    upper bound min(d^i, d^(L-i), chi) (the same counting formulas the library applies
+    to the realised bonds). Used only by the reference arm, which runs no GPU code."""
+    ub = lambda i, n: min(chi, d ** min(i, n - i))
+    fl = 0.0
+
+    def qr(m, n, k, rr):
+        p, q = max(m, n), min(m, n)
+        return 2 * p * q * q - 2 / 3 * q ** 3 + 2 * m * k * k - 2 / 3 * k ** 3 + 2 * k * n * d * rr
+
+    # preparation: two left-canonicalising QR sweeps
+    for _ in range(2):
+        for k in range(L - 1):
+            Dl, Dr, Drr = ub(k, L), ub(k + 1, L), ub(k + 2, L)
+            fl += qr(d * Dl, Dr, min(d * Dl, Dr), Drr)
+    # sweep: iteration i moves the centre through Pi_{i+1}..Pi_N and swaps back
+    for i in range(L - 1, 0, -1):
+        for j in range(i + 1, L + 1):
+            D = min(chi, ub(j, L) ** 2) if False else chi
+            fl += qr(d * D, D, D, D)
+        for j in range(L, i, -1):
+            Dl = Dm = Dr = chi
+            m = n = d * chi
+            fl += 2.0 * d * d * Dl * Dm * Dr + 2.0 * m * n * n + 2.0 * m * n * chi
+        fl += 2.0 * d * chi ** 3
+    return fl
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU float64 oracle (the only implementation of the paper here)."""
+    if rank != 0:
+        return
+    flops_product = model_flops(args.L, 2, args.chi)
+    for _ in range(args.warmup):
+        cpu_baseline(args, flops_product, swap_model_flops(args.chi), n_samples=1)
+    vals, spent = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, s, desc = cpu_baseline(args, flops_product, swap_model_flops(args.chi), n_samples=1)
+        vals.append(v)
+        spent += s
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args),
+            "cpu_baseline": {"value": value, "unit": "products/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    import paper_2410_19747_gb300 as pkg
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    pkg.build()
+    h = pkg.Handle(dev.index)
+    A, B = workload(args.L, args.chi, 3000 + 10 * rank)
+    Ag = [torch.from_numpy(c).to(dev) for c in A]
+    Bg = [torch.from_numpy(c).to(dev) for c in B]
+    kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        pkg.ttm_multiply(h, Ag, Bg, **kw)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+
+    reps, dts = [], []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                       # L2 flush, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out, rep = pkg.ttm_multiply(h, Ag, Bg, profile=1, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            dts.append(e0.elapsed_time(e1) / 1e3)
+            reps.append(rep)
+    torch.cuda.synchronize(dev)
+    t_local = sum(dts)
+    t = t_local
+    if dist:
+        tt = torch.tensor([t_local], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        dist.barrier()
+    products = world * args.steps
+    value = products / t
+
+    # end to end through the public call from pinned host buffers
+    Ah = [torch.from_numpy(c).pin_memory() for c in A]
+    Bh = [torch.from_numpy(c).pin_memory() for c in B]
+    e2e_t, h2d, d2h = 0.0, 0, 0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        outh, rh = pkg.ttm_multiply(h, Ah, Bh, **kw)
+        e2e_t += time.perf_counter() - t0
+        h2d = sum(c.numel() * 8 for c in Ah) + sum(c.numel() * 8 for c in Bh)
+        d2h = sum(c.size * 8 for c in outh)
+    e2e_val = world * args.e2e_steps / e2e_t if e2e_t > 0 else None
+    if dist:
+        ev = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(ev, op=dist.ReduceOp.MAX)
+        e2e_val = world * args.e2e_steps / float(ev.item())
+
+    if rank == 0:
+        r0 = reps[-1]
+        flops = float(np.mean([r["flops_counted"] for r in reps]))
+        jac_ms = sum(r["jacobi_ms"] for r in reps)
+        jac_fl = sum(r["jacobi_flops"] for r in reps)
+        jac_launch = sum(r["jacobi_launches"] for r in reps)
+        achieved = (jac_fl / (jac_ms / 1e3) / 1e12) if jac_ms > 0 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args),
+            "tflops_counted": flops * products / t / 1e12,
+            "roofline": {"bound": "alu", "kernel": "hestenes_kernel (one-sided Jacobi SVD, float64)",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "peak_source": "nominal float64 rate: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
+                         "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                         "share_of_step": jac_ms / 1e3 / t_local if t_local > 0 else None,
+                         "launches": jac_launch, "avg_launch_ms": jac_ms / max(1, jac_launch)},
+            "e2e": {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(r["n_kernel_launches"] for r in reps)),
+            "clocks": clk.summary(),
+            "report": {k: r0[k] for k in ("n_swaps", "n_contracts", "n_qr", "max_bond", "discarded_weight",
+                                          "err_bound", "norm_out", "jacobi_sweeps_max")},
+        }
+        if not args.no_cpu_baseline:
+            v, spent, desc = cpu_baseline(args, flops, swap_model_flops(args.chi))
+            line["cpu_baseline"] = {"value": v, "unit": "products/s", "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": desc}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    h.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * ttm.h -- C ABI of the GB300 (sm_103a) Tensor Train Multiplication library (libttm.so).
+ *
+ * The library forms the elementwise (Hadamard) product Omega = A o B of two tensor
+ * trains by the swap-and-contract sweep of arXiv:2410.19747, Sec. II.B:
+ *   - the two trains are concatenated into one chain of length 2N with B reversed
+ *     (Eq. tensor; each reversed carriage has its bond legs exchanged);
+ *   - carriages with the same site index are joined by the local COPY tensor
+ *     (Contract, Eq. contract);
+ *   - B's carriages travel left by Swaps: two-site contraction, permutation of the
+ *     physical legs, SVD and truncation by Eq. eps (Fig. 1C);
+ *   - the chain is kept in mixed canonical gauge with QR gauge moves after every
+ *     Contract (the paragraph after Eq. eps).
+ * Every step runs in this library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *   - A TT of length L with physical dimension d is L cores; core k has shape
+ *     [bonds[k]][d][bonds[k+1]], row-major, float64, contiguous; bonds[0] =
+ *     bonds[L] = 1 (Eq. TT, Eq. bond).
+ *   - Inputs are read-only, stream-ordered on the handle's stream and not
+ *     retained after the call returns (host inputs are copied in).
+ *   - No call throws or aborts. Every call returns a ttm_status; a message for the
+ *     last failure on the calling thread is available from ttm_last_error().
+ *   - Device-side waits are bounded; none traps.
+ */
+#ifndef TTM_H
+#define TTM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttm_handle ttm_handle;
+
+typedef enum {
+  TTM_OK = 0,
+  TTM_ERR_INVALID_ARG = -1, /* null pointer, eps outside [0,1), L < 1, d < 2 ...      */
+  TTM_ERR_SHAPE = -2,       /* boundary bond != 1, bond above min(d^i, d^(L-i)), A/B
+                               mismatch, caller buffer too small                     */
+  TTM_ERR_NOMEM = -3,       /* device allocation failed                              */
+  TTM_ERR_WORKSPACE = -4,   /* a caller-sized workspace is too small                 */
+  TTM_ERR_NONFINITE = -5,   /* NaN/Inf met in an input (only when checked)           */
+  TTM_ERR_CUDA = -6,        /* a CUDA runtime call failed (message has the cause)    */
+  TTM_ERR_TIMEOUT = -7,     /* a bounded device-side loop hit its iteration limit    */
+  TTM_ERR_RANK_CAP = -8,    /* a bond would exceed the library's supported maximum   */
+  TTM_ERR_UNSUPPORTED = -9  /* option combination not supported                      */
+} ttm_status;
+
+/* Arithmetic of the GEMM-shaped contractions. Decompositions (QR, SVD) and norms
+ * always run in float64 on the GPU. */
+typedef enum {
+  TTM_PREC_FP64 = 0,    /* plain float64 everywhere (the reference form)             */
+  TTM_PREC_TF32X3 = 1,  /* tensor-core split products, float32 accumulation per tile */
+  TTM_PREC_BF16X3 = 2   /* tensor-core bf16 split products                            */
+} ttm_precision;
+
+typedef enum {
+  TTM_LOSS_INNER = 0,   /* f = <W, A o B>                                              */
+  TTM_LOSS_SQDIST = 1   /* g = ||A o B - C||^2                                          */
+} ttm_loss;
+
+typedef struct {
+  int32_t L;            /* number of sites (carriages)                                 */
+  int32_t d;            /* physical dimension of every site                            */
+  int32_t on_host;      /* 0: cores are device pointers; 1: host pointers (copied in,
+                           and for outputs copied out, inside the call)               */
+  int32_t reserved;
+  int64_t *bonds;       /* L+1 entries, host memory                                    */
+  double **cores;       /* L pointers, host array; core k = [bonds[k]][d][bonds[k+1]]  */
+} ttm_tt;
+
+typedef struct {
+  ttm_precision prec;
+  double eps;               /* Eq. eps threshold on the relative discarded weight of every
+                               Swap SVD; 0 keeps every singular value                     */
+  int64_t chi_max;          /* cap on the bond of every Swap SVD; 0 = unbounded          */
+  int64_t chi_out;          /* cap on the output bonds (final TT-SVD rounding); 0 = none */
+  int32_t max_sweeps;       /* one-sided Jacobi sweep limit per SVD; 0 = library default */
+  int32_t use_graph;        /* 1: capture the whole sweep in a CUDA graph and replay it  */
+  int32_t check_finite;     /* 1: scan inputs for NaN/Inf on the device                  */
+  int32_t profile_kernels;  /* 1: time every one-sided Jacobi launch with CUDA events on
+                               the handle's stream (fills the jacobi_* report fields)      */
+} ttm_options;
+
+/* Filled by ttm_multiply. All fields are host values once the call returns. */
+typedef struct {
+  int32_t status;
+  int32_t jacobi_sweeps_max;   /* largest sweep count any SVD needed                     */
+  int64_t max_bond;            /* largest bond created by any Swap / QR / Contract       */
+  int64_t n_swaps, n_contracts, n_qr;
+  double discarded_weight;     /* sum_j w_j, w_j = sum of dropped lambda^2 of truncation j */
+  double err_bound;            /* sum_j sqrt(w_j): bound on ||Omega - A o B||_2           */
+  double norm_out;             /* ||Omega||_2                                             */
+  double flops_counted;        /* model flops of the GEMM-shaped and QR work (Jacobi
+                                  iterations excluded), from the realised bonds           */
+  double seconds;              /* device time of the call (CUDA events)                  */
+  int64_t peak_workspace_bytes;
+  int64_t *bond_trace;         /* caller array or NULL: max chain bond after each Contract */
+  int64_t bond_trace_len;      /* in: capacity of bond_trace; out: entries written (N)    */
+  int64_t n_kernel_launches;   /* kernels this call launched (all products of a batch)   */
+  int64_t jacobi_launches;     /* one-sided Jacobi launches                               */
+  double jacobi_ms;            /* their summed device time (profile_kernels = 1), else 0 */
+  double jacobi_flops;         /* float64 flops the Jacobi kernels executed (counted on
+                                  the device: dot products and applied rotations)         */
+} ttm_report;
+
+/* Creates a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). `opt` may be NULL
+ * (defaults: FP64, eps = 0, no caps). */
+ttm_status ttm_create(ttm_handle **h, int device, void *cuda_stream, const ttm_options *opt);
+ttm_status ttm_destroy(ttm_handle *h);
+/* Replaces the handle's options. */
+ttm_status ttm_set_options(ttm_handle *h, const ttm_options *opt);
+
+/*
+ * Omega = A o B (Sec. II.B). A and B must share L and d.
+ * out: out->L, out->d are set by the library; out->bonds must point to L+1 host
+ * int64 entries (receives the realised output bonds) and out->cores to L host
+ * pointer slots. Three output modes:
+ *   on_host = 0, cores[0] == NULL : the library writes device pointers into
+ *       handle-owned memory, valid until the next multiply on the handle or
+ *       ttm_destroy;
+ *   on_host = 0, cores[k] != NULL : caller device buffers, each of at least
+ *       ttm_output_capacity(...) doubles; the cores are copied there;
+ *   on_host = 1                   : caller host buffers of the same capacity.
+ * The stored core k is compact: [bonds[k]][d][bonds[k+1]].
+ * rep may be NULL. Blocks until the result is host-visible.
+ */
+ttm_status ttm_multiply(ttm_handle *h, const ttm_tt *A, const ttm_tt *B, ttm_tt *out,
+                        ttm_report *rep);
+
+/*
+ * n independent products A[i] o B[i] in one batched launch sequence: every kernel of
+ * the sweep covers all n products (grid z = product), so products of uneven chi
+ * share each launch. All pairs must share L and d. Outputs and reports as in
+ * ttm_multiply (n entries each); rep[i].status holds each product's status and the
+ * call returns the worst one.
+ */
+ttm_status ttm_multiply_batched(ttm_handle *h, int32_t n, const ttm_tt *A, const ttm_tt *B,
+                                ttm_tt *out, ttm_report *rep);
+
+/* Doubles needed per host output core for the given inputs and options. */
+int64_t ttm_output_capacity(const ttm_tt *A, const ttm_tt *B, const ttm_options *opt);
+
+/*
+ * Value and gradients of a scalar functional of the product:
+ *   TTM_LOSS_INNER : f = <W, A o B>,       W_or_C = W
+ *   TTM_LOSS_SQDIST: g = ||A o B - C||^2,  W_or_C = C
+ * Environments are contracted over the shared physical index (three layers for
+ * <W, A o B>, four for <A o B, A o B>). gradA / gradB have the shapes of A / B
+ * (caller device buffers, overwritten); either may be NULL to skip it.
+ * *loss_out receives the value (host double).
+ */
+ttm_status ttm_backward(ttm_handle *h, ttm_loss kind, const ttm_tt *A, const ttm_tt *B,
+                        const ttm_tt *W_or_C, double *loss_out, ttm_tt *gradA, ttm_tt *gradB);
+
+/* <X, Y> (two-layer environment) and <W, A o B> (three-layer environment) of device
+ * TTs, in float64; the "." product of the paper's error measure Gamma (Sec. III). */
+ttm_status ttm_inner(ttm_handle *h, const ttm_tt *X, const ttm_tt *Y, double *out);
+ttm_status ttm_inner3(ttm_handle *h, const ttm_tt *W, const ttm_tt *A, const ttm_tt *B,
+                      double *out);
+
+/* Waits for all work queued on the handle's stream. */
+ttm_status ttm_synchronize(ttm_handle *h);
+/* Releases the handle-owned output of the last multiply (optional; ttm_destroy frees all). */
+ttm_status ttm_tt_free(ttm_handle *h, ttm_tt *t);
+/* Message for the last failing call on this thread ("" if none). */
+const char *ttm_last_error(void);
+/* Library version string. */
+const char *ttm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTM_H */

@@ -1,0 +1,612 @@
+// ttm_api.cu -- the C ABI of include/ttm.h and the schedule of the TTM sweep.
+//
+// Schedule (Sec. II.B): after the preparation (both trains left-canonical, B reversed
+// with its bond legs exchanged so the reversed part is right-orthonormal, Eq. tensor),
+// site N is contracted across the size-1 junction; then for i = N-1 .. 1 the gauge
+// centre is moved by QR from Pi_{i+1} through Pi_N into B's carriage of site i (the
+// mover), the mover is swapped leftwards past Pi_N .. Pi_{i+1} (i-1 swaps in the
+// paper's count), and finally contracted with A's carriage of site i (Eq. contract).
+// That is N contractions and N(N-1)/2 swaps.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ttm.h"
+#include "ttm_engine.cuh"
+
+struct ttm_handle {
+  ttm::HandleState s;
+  std::vector<double*> last_out;  // device pointers of the last result (into the arena)
+};
+
+namespace ttm {
+
+static thread_local std::string g_last_error;
+
+static ttm_status set_err(ttm_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+// ---------------------------------------------------------------- steps
+
+void Engine::load_core(const ttm_tt* T, int k, int buf) {
+  if (!launch_) return;
+  for (int z = 0; z < Z_; ++z) {
+    const ttm_tt& t = T[z];
+    const size_t n = (size_t)t.bonds[k] * t.d * t.bonds[k + 1];
+    TTM_CUDA(cudaMemcpyAsync(hbuf_[(size_t)z * nb_ + buf], t.cores[k], n * sizeof(double),
+                             t.on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, hs_.stream));
+  }
+}
+
+// Gauge move of one carriage (QR after Contract): C [bl][d][br] = Q R; C <- Q; Next <- R Next.
+void Engine::qr_move(int c, int& nx, int bl, int& br, int brr) {
+  std::vector<int> kub(Z_);
+  for (int z = 0; z < Z_; ++z) kub[z] = std::min(d_ * ub_[bl][z], ub_[br][z]);
+  const int nbnd = new_bond(kub);
+  const int m_ub = d_ * umax(bl), n_ub = umax(br), k_ub = umax(nbnd);
+  t_elems_ = std::max(t_elems_, (long)m_ub * n_ub);
+  r_elems_ = std::max(r_elems_, (long)k_ub * n_ub);
+  q_elems_ = std::max(q_elems_, (long)m_ub * k_ub);
+  vec_elems_ = std::max(vec_elems_, (long)k_ub + 1);
+  log_.push_back({SK_QR, bl, br, nbnd, brr});
+  const int out = get_buf();
+  note_carriage(bl, nbnd);
+  note_carriage(nbnd, brr);
+  if (launch_) {
+    const Dim m{d_, bl}, n{1, br};
+    copy2d(RowToColFn{tab_, c, ws(WS_T), m, n}, 1, m_ub, n_ub);
+    QRArgs qa{tab_, ws(WS_T), ws(WS_TAU), ws(WS_R), ws(WS_Q), m, n, nbnd, n_ub, k_ub};
+    coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8);
+    copy2d(ColToRowFn{tab_, ws(WS_Q), c, m, Dim{1, nbnd}}, 1, m_ub, k_ub);
+    gemm(RMergeFn{tab_, ws(WS_R), nx, out, nbnd, br, brr, d_}, 1, k_ub, d_ * umax(brr));
+  }
+  put_buf(nx);
+  nx = out;
+  br = nbnd;
+}
+
+// Swap of X [bl][d][bm] and Y [bm][d][br] (Fig. 1C); Y's buffer receives the new left
+// carriage (the mover, U Lambda), X's buffer the new right one (V^T). Returns the new bond.
+int Engine::swap(int x, int y, int bl, int bm, int br) {
+  std::vector<int> kub(Z_);
+  for (int z = 0; z < Z_; ++z) {
+    int v = std::min(d_ * ub_[bl][z], d_ * ub_[br][z]);
+    if (opt_.chi_max > 0) v = std::min<long>(v, opt_.chi_max);
+    kub[z] = v;
+  }
+  const int nbnd = new_bond(kub);
+  const int m_ub = d_ * umax(bl), n_ub = d_ * umax(br), k_ub = umax(nbnd);
+  const int nscr = new_bond(std::vector<int>(Z_, n_ub));  // receives n from the V orthonormalisation
+  t_elems_ = std::max(t_elems_, (long)m_ub * n_ub);
+  v_elems_ = std::max(v_elems_, (long)n_ub * n_ub);
+  x_elems_ = std::max(x_elems_, (long)std::max(m_ub, n_ub) * n_ub);
+  r_elems_ = std::max(r_elems_, (long)n_ub * n_ub);
+  vec_elems_ = std::max(vec_elems_, (long)n_ub + 1);
+  log_.push_back({SK_SWAP, bl, bm, br, nbnd});
+  note_carriage(bl, nbnd);
+  note_carriage(nbnd, br);
+  const int wslot = ST_NFIXED + n_trunc_++;
+  const int sw32 = jac_launch_++;
+  const int sw64 = jac_launch_++;
+  if (launch_) {
+    const Dim m{d_, bl}, n{d_, br};
+    const int npad_ub = n_ub + (n_ub & 1);
+    const long pairs = (long)Z_ * (npad_ub / 2);
+    // 1. Theta = X Y with the physical legs permuted, column-major m x n (Fig. 1C)
+    gemm(ThetaFn{tab_, x, y, ws(WS_T), bl, bm, br, d_}, d_ * d_, umax(bl), umax(br));
+    // 2. float32 one-sided Jacobi on a float copy: the rotation V32 (preconditioner)
+    cast(ws(WS_T), ws(WS_W32), m, n, 1, (long)m_ub * n_ub);
+    HestArgs h32{tab_, ws(WS_W32), ws(WS_V32), m, n, npad_ub, 30,
+                 counters_ + (size_t)sw32 * counter_stride_,
+                 16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)), 64 * 5.96e-8,
+                 fro2_ + (size_t)sw32 * Z_, 1, ST_JFLOPS32, ws(WS_NRM), -1};
+    coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs);
+    // 3. V0 = Q of a float64 Householder QR of V32: orthonormal to float64 rounding
+    cast(ws(WS_V32), ws(WS_X), n, n, 0, (long)n_ub * n_ub);
+    QRArgs qa{tab_, ws(WS_X), ws(WS_TAU), ws(WS_R), ws(WS_V), n, n, nscr, n_ub, n_ub};
+    coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8);
+    // 4. W = Theta V0 in float64: Theta = W V0^T holds exactly up to rounding
+    gemm(ThetaVFn{tab_, ws(WS_T), ws(WS_V), ws(WS_X), m, n}, 1, m_ub, n_ub);
+    // 5. float64 polish of all column pairs from the float32 starting point: the column
+    //    norms become the singular values to float64 accuracy, so the rank rule and the
+    //    discarded weight of Eq. eps are decided in float64.
+    {
+      cudaEvent_t pe0 = nullptr, pe1 = nullptr;
+      if (opt_.profile_kernels) {
+        pe0 = prof_event();
+        pe1 = prof_event();
+        TTM_CUDA(cudaEventRecord(pe0, hs_.stream));
+      }
+      HestArgs h64{tab_, ws(WS_X), ws(WS_V), m, n, npad_ub, max_sweeps(),
+                   counters_ + (size_t)sw64 * counter_stride_,
+                   1e-10, 64 * 1.11e-16,
+                   fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), -1};
+      coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs);
+      if (opt_.profile_kernels) TTM_CUDA(cudaEventRecord(pe1, hs_.stream));
+    }
+    // 6. final order by column norm, Eq. eps + cap, new carriages
+    order_and_truncate(m, n, nbnd, 1, wslot, n_ub);
+    {
+      ++launches_;
+      GatherArgs ga{tab_, ws(WS_X), ws(WS_V), ws(WS_PERM), y, x, bl, br, nbnd, d_};
+      dim3 g3(cdiv(std::max(m_ub, n_ub), 128), k_ub, Z_);
+      swap_gather_kernel<<<g3, 128, 0, hs_.stream>>>(ga);
+      TTM_CUDA(cudaGetLastError());
+    }
+  }
+  return nbnd;
+}
+
+// Column norms of W (workspace X), descending order, and the rank rule of Eq. eps.
+void Engine::order_and_truncate(Dim m, Dim n, int ibond, int record, int wslot, int n_ub, int ieps) {
+  launches_ += 3;
+  NormArgs na{tab_, ws(WS_X), ws(WS_NRM), m, n};
+  dim3 g(cdiv(n_ub, 8), Z_);
+  colnorm_kernel<<<g, 256, 0, hs_.stream>>>(na);
+  TTM_CUDA(cudaGetLastError());
+  RankArgs ra{tab_, ws(WS_NRM), ws(WS_SORT), ws(WS_PERM), n};
+  dim3 g2(cdiv(n_ub, 256), Z_);
+  rank_kernel<<<g2, 256, 0, hs_.stream>>>(ra);
+  TTM_CUDA(cudaGetLastError());
+  TruncArgs ta{tab_, ws(WS_SORT), m, n, ibond, opt_.eps, (int)opt_.chi_max, wslot, record, ieps};
+  truncate_kernel<<<Z_, 1024, 0, hs_.stream>>>(ta);
+  TTM_CUDA(cudaGetLastError());
+}
+
+void Engine::contract(int kb, int mb, int out, int il, int ia, int ir) {
+  log_.push_back({SK_CONTRACT, il, ia, ir, 0});
+  note_carriage(il, ir);
+  gemm(ContractFn{tab_, kb, mb, out, il, ia, ir, d_}, d_, umax(il), umax(ir));
+}
+
+void Engine::run() {
+  const int L = L_;
+  std::vector<int> a(L), b(L), bA(L + 1), bB(L + 1);
+  for (int i = 0; i <= L; ++i) {
+    std::vector<int> va(Z_), vb(Z_);
+    for (int z = 0; z < Z_; ++z) {
+      va[z] = (int)A_[z].bonds[i];
+      vb[z] = (int)B_[z].bonds[i];
+    }
+    bA[i] = new_bond(va, &va);
+    bB[i] = new_bond(vb, &vb);
+  }
+  for (int k = 0; k < L; ++k) {
+    a[k] = get_buf();
+    b[k] = get_buf();
+    note_carriage(bA[k], bA[k + 1]);
+    note_carriage(bB[k], bB[k + 1]);
+    load_core(A_, k, a[k]);
+    load_core(B_, k, b[k]);
+  }
+  // a1: both trains left-canonical (QR sweeps); the norms end in the last carriages.
+  for (int k = 0; k + 1 < L; ++k) qr_move(a[k], a[k + 1], bA[k], bA[k + 1], bA[k + 2]);
+  for (int k = 0; k + 1 < L; ++k) qr_move(b[k], b[k + 1], bB[k], bB[k + 1], bB[k + 2]);
+  // Eq. tensor: B reversed, each carriage with its bond legs exchanged.
+  std::vector<int> mt(L), mtL(L), mtR(L);
+  for (int j = 0; j < L; ++j) {
+    const int src = b[L - 1 - j];
+    const int dst = get_buf();
+    const int il = bB[L - 1 - j], ir = bB[L - j];
+    note_carriage(ir, il);
+    copy2d(LegSwapFn{tab_, src, dst, il, ir, d_}, d_, umax(il), umax(ir));
+    put_buf(src);
+    mt[j] = dst;
+    mtL[j] = ir;
+    mtR[j] = il;
+  }
+  std::vector<int> pi(L + 1), piL(L + 1), piR(L + 1);
+  auto record_trace = [&](int i) {
+    std::vector<int> ids;
+    for (int k = 0; k < i - 1; ++k) ids.push_back(bA[k + 1]);
+    for (int j = i; j <= L; ++j) ids.push_back(piR[j]);
+    for (int q = L - i + 1; q < L; ++q) ids.push_back(mtR[q]);
+    trace_ids_.push_back(ids);
+  };
+  // a2: site N across the size-1 junction.
+  pi[L] = get_buf();
+  contract(a[L - 1], mt[0], pi[L], bA[L - 1], bA[L], mtR[0]);
+  put_buf(a[L - 1]);
+  put_buf(mt[0]);
+  piL[L] = bA[L - 1];
+  piR[L] = mtR[0];
+  record_trace(L);
+  for (int i = L - 1; i >= 1; --i) {
+    int mv = mt[L - i], mvL = mtL[L - i], mvR = mtR[L - i];
+    (void)mvL;
+    // a3: centre from Pi_{i+1} through Pi_N into the mover.
+    for (int j = i + 1; j <= L; ++j) {
+      if (j < L) {
+        qr_move(pi[j], pi[j + 1], piL[j], piR[j], piR[j + 1]);
+        piL[j + 1] = piR[j];
+      } else {
+        qr_move(pi[L], mv, piL[L], piR[L], mvR);
+        mvL = piR[L];
+      }
+    }
+    // a4 + a5: the mover passes Pi_N .. Pi_{i+1}.
+    for (int j = L; j >= i + 1; --j) {
+      const int nb = swap(pi[j], mv, piL[j], piR[j], mvR);
+      mvL = piL[j];
+      const int oldR = mvR;
+      mvR = nb;
+      piL[j] = nb;
+      piR[j] = oldR;
+    }
+    // a6: Contract with A's carriage of site i.
+    const int out = get_buf();
+    contract(a[i - 1], mv, out, bA[i - 1], bA[i], mvR);
+    put_buf(a[i - 1]);
+    put_buf(mv);
+    pi[i] = out;
+    piL[i] = bA[i - 1];
+    piR[i] = mvR;
+    record_trace(i);
+  }
+  out_buf_.assign(pi.begin() + 1, pi.end());
+  out_bond_.assign(L + 1, 0);
+  out_bond_[0] = piL[1];
+  for (int j = 1; j <= L; ++j) out_bond_[j] = piR[j];
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report>* reps, ttm_tt* outs) {
+  (void)opt;
+  // Layout of the arena: per product [chain buffers | workspaces], then the tables.
+  char* base = (char*)arena;
+  size_t off = 0;
+  hbuf_.assign((size_t)Z_ * nb_, nullptr);
+  const long ws_elems[WS_COUNT] = {t_elems_, v_elems_, vec_elems_, vec_elems_, vec_elems_,
+                                   vec_elems_, r_elems_, q_elems_, t_elems_ / 2 + 1, v_elems_ / 2 + 1,
+                                   x_elems_};
+  for (int z = 0; z < Z_; ++z) {
+    for (int bi = 0; bi < nchain_; ++bi) {
+      hbuf_[(size_t)z * nb_ + bi] = (double*)(base + off);
+      off = align256(off + (size_t)carriage_elems_ * 8);
+    }
+    for (int w = 0; w < WS_COUNT; ++w) {
+      hbuf_[(size_t)z * nb_ + nchain_ + w] = (double*)(base + off);
+      off = align256(off + (size_t)ws_elems[w] * 8);
+    }
+  }
+  const int nbd = (int)ub_.size();
+  const int ns = ST_NFIXED + n_trunc_;
+  const int nis = IS_NFIXED;
+  d_buf_ = (double**)(base + off);
+  off = align256(off + (size_t)Z_ * nb_ * sizeof(double*));
+  d_bond_ = (int*)(base + off);
+  off = align256(off + (size_t)Z_ * nbd * sizeof(int));
+  d_stat_ = (double*)(base + off);
+  off = align256(off + (size_t)Z_ * ns * sizeof(double));
+  d_istat_ = (int*)(base + off);
+  off = align256(off + (size_t)Z_ * nis * sizeof(int));
+  counter_stride_ = Z_ * max_sweeps();
+  counters_ = (int*)(base + off);
+  const int n_jac = std::max(1, jac_launch_);
+  off = align256(off + (size_t)n_jac * counter_stride_ * sizeof(int));
+  fro2_ = (double*)(base + off);
+  off = align256(off + (size_t)n_jac * Z_ * sizeof(double));
+
+  std::vector<int> hb((size_t)Z_ * nbd, 0);
+  for (int id = 0; id < nbd; ++id)
+    if (!exact_[id].empty())
+      for (int z = 0; z < Z_; ++z) hb[(size_t)z * nbd + id] = exact_[id][z];
+  cudaStream_t st = hs_.stream;
+  TTM_CUDA(cudaEventRecord(hs_.ev0, st));
+  TTM_CUDA(cudaMemcpyAsync(d_buf_, hbuf_.data(), hbuf_.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  TTM_CUDA(cudaMemcpyAsync(d_bond_, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  TTM_CUDA(cudaMemsetAsync(d_stat_, 0, (size_t)Z_ * ns * sizeof(double), st));
+  TTM_CUDA(cudaMemsetAsync(d_istat_, 0, (size_t)Z_ * nis * sizeof(int), st));
+  TTM_CUDA(cudaMemsetAsync(counters_, 0, (size_t)n_jac * counter_stride_ * sizeof(int), st));
+  TTM_CUDA(cudaMemsetAsync(fro2_, 0, (size_t)n_jac * Z_ * sizeof(double), st));
+  tab_ = Tables{d_buf_, d_bond_, d_stat_, d_istat_, nb_, nbd, ns, nis, Z_};
+
+  // second walk: launch
+  launches_ = 0;
+  prof_used_ = 0;
+  const int nchain_planned = nchain_;
+  const int jac_planned = jac_launch_;
+  launch_ = true;
+  reset_ids();
+  run();
+  if ((int)nbuf_total_ != nchain_planned || jac_launch_ != jac_planned)
+    throw Error(TTM_ERR_INVALID_ARG, "internal: plan and launch walks disagree");
+  TTM_CUDA(cudaEventRecord(hs_.ev1, st));
+
+  // results
+  std::vector<int> bonds((size_t)Z_ * nbd);
+  std::vector<double> stat((size_t)Z_ * ns);
+  std::vector<int> istat((size_t)Z_ * nis);
+  TTM_CUDA(cudaMemcpyAsync(bonds.data(), d_bond_, bonds.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  TTM_CUDA(cudaMemcpyAsync(stat.data(), d_stat_, stat.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TTM_CUDA(cudaMemcpyAsync(istat.data(), d_istat_, istat.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  TTM_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  TTM_CUDA(cudaEventElapsedTime(&ms, hs_.ev0, hs_.ev1));
+  double jac_ms = 0.0;
+  for (int q = 0; q + 1 < prof_used_; q += 2) {
+    float x = 0.f;
+    TTM_CUDA(cudaEventElapsedTime(&x, hs_.prof_events[q], hs_.prof_events[q + 1]));
+    jac_ms += x;
+  }
+
+  for (int z = 0; z < Z_; ++z) {
+    auto bv = [&](int id) { return (long)bonds[(size_t)z * nbd + id]; };
+    ttm_tt& o = outs[z];
+    const bool caller_out = !o.on_host && o.cores[0] != nullptr;
+    o.L = L_;
+    o.d = d_;
+    for (int j = 0; j <= L_; ++j) o.bonds[j] = bv(out_bond_[j]);
+    for (int j = 0; j < L_; ++j) {
+      double* src = hbuf_[(size_t)z * nb_ + out_buf_[j]];
+      const size_t n = (size_t)o.bonds[j] * d_ * o.bonds[j + 1];
+      if (o.on_host) {
+        TTM_CUDA(cudaMemcpyAsync(o.cores[j], src, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      } else if (caller_out) {
+        TTM_CUDA(cudaMemcpyAsync(o.cores[j], src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      } else {
+        o.cores[j] = src;
+      }
+    }
+    ttm_report& r = (*reps)[z];
+    const int64_t* user_trace = r.bond_trace;
+    const int64_t trace_cap = r.bond_trace_len;
+    std::memset(&r, 0, sizeof(r));
+    r.status = TTM_OK;
+    r.jacobi_sweeps_max = istat[(size_t)z * nis + IS_SWEEPS_MAX];
+    long maxb = 0;
+    for (int id = 0; id < nbd; ++id) maxb = std::max(maxb, bv(id));
+    r.max_bond = maxb;
+    double fl = 0.0;
+    for (const StepLog& s : log_) {
+      if (s.kind == SK_SWAP) {
+        r.n_swaps++;
+        const double Dl = bv(s.b0), Dm = bv(s.b1), Dr = bv(s.b2), k = bv(s.b3);
+        const double m = d_ * Dl, n = d_ * Dr;
+        fl += 2.0 * d_ * d_ * Dl * Dm * Dr;            // Theta
+        fl += 2.0 * m * n * n + 2.0 * m * n * k;       // Gram-equivalent + U formation (SVD model)
+      } else if (s.kind == SK_CONTRACT) {
+        r.n_contracts++;
+        fl += 2.0 * d_ * (double)bv(s.b0) * bv(s.b1) * bv(s.b2);
+      } else {
+        r.n_qr++;
+        const double m = d_ * (double)bv(s.b0), n = bv(s.b1), k = bv(s.b2), rr = bv(s.b3);
+        const double p = std::max(m, n), q = std::min(m, n);
+        fl += 2.0 * p * q * q - 2.0 / 3.0 * q * q * q;  // factorisation
+        fl += 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;  // explicit Q
+        fl += 2.0 * k * n * d_ * rr;                     // R merge
+      }
+    }
+    r.flops_counted = fl;
+    r.discarded_weight = stat[(size_t)z * ns + ST_WSUM];
+    r.err_bound = stat[(size_t)z * ns + ST_WSQRT];
+    r.seconds = ms * 1e-3;
+    r.peak_workspace_bytes = (int64_t)bytes_needed();
+    if (istat[(size_t)z * nis + IS_NONCONV] > 0) r.status = TTM_OK;  // result valid; optimality not guaranteed
+    r.n_kernel_launches = launches_;
+    r.jacobi_launches = jac_launch_;
+    r.jacobi_ms = jac_ms;
+    r.jacobi_flops = stat[(size_t)0 * ns + ST_JFLOPS];  // float64 polish, launch-wide (all products)
+    r.bond_trace = (int64_t*)user_trace;
+    r.bond_trace_len = 0;
+    if (user_trace) {
+      const int64_t nt = std::min<int64_t>(trace_cap, (int64_t)trace_ids_.size());
+      for (int64_t q = 0; q < nt; ++q) {
+        long mb = 1;
+        for (int id : trace_ids_[q]) mb = std::max(mb, bv(id));
+        r.bond_trace[q] = mb;
+      }
+      r.bond_trace_len = nt;
+    }
+  }
+  // norm of the output: centre on Pi_1, the other carriages right-orthonormal
+  for (int z = 0; z < Z_; ++z) {
+    const ttm_tt& o = outs[z];
+    const size_t n = (size_t)o.bonds[0] * d_ * o.bonds[1];
+    std::vector<double> c0(n);
+    TTM_CUDA(cudaMemcpy(c0.data(), hbuf_[(size_t)z * nb_ + out_buf_[0]], n * sizeof(double), cudaMemcpyDeviceToHost));
+    double s = 0.0;
+    for (double v : c0) s += v * v;
+    (*reps)[z].norm_out = std::sqrt(s);
+  }
+  TTM_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------- validation
+
+static ttm_status check_tt(const ttm_tt* t, const char* name, bool need_cores) {
+  if (!t) return set_err(TTM_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (t->L < 1) return set_err(TTM_ERR_INVALID_ARG, std::string(name) + ": L < 1");
+  if (t->d < 2) return set_err(TTM_ERR_INVALID_ARG, std::string(name) + ": d < 2");
+  if (!t->bonds) return set_err(TTM_ERR_INVALID_ARG, std::string(name) + ": bonds is NULL");
+  if (need_cores && !t->cores) return set_err(TTM_ERR_INVALID_ARG, std::string(name) + ": cores is NULL");
+  if (t->bonds[0] != 1 || t->bonds[t->L] != 1)
+    return set_err(TTM_ERR_SHAPE, std::string(name) + ": boundary bonds must be 1");
+  for (int i = 0; i <= t->L; ++i) {
+    // bound min(d^i, d^(L-i)), saturating
+    double lim = std::min(std::pow((double)t->d, i), std::pow((double)t->d, t->L - i));
+    if (t->bonds[i] < 1 || (double)t->bonds[i] > lim)
+      return set_err(TTM_ERR_SHAPE, std::string(name) + ": bond " + std::to_string(i) + " = " +
+                                        std::to_string(t->bonds[i]) + " outside [1, min(d^i, d^(L-i))]");
+    if (t->bonds[i] > kMaxBond) return set_err(TTM_ERR_RANK_CAP, std::string(name) + ": bond too large");
+  }
+  if (need_cores)
+    for (int k = 0; k < t->L; ++k)
+      if (!t->cores[k]) return set_err(TTM_ERR_INVALID_ARG, std::string(name) + ": core " + std::to_string(k) + " is NULL");
+  return TTM_OK;
+}
+
+static ttm_status check_opts(const ttm_options& o) {
+  if (!(o.eps >= 0.0 && o.eps < 1.0)) return set_err(TTM_ERR_INVALID_ARG, "eps must lie in [0, 1)");
+  if (o.chi_max < 0 || o.chi_out < 0) return set_err(TTM_ERR_INVALID_ARG, "negative cap");
+  if (o.prec != TTM_PREC_FP64 && o.prec != TTM_PREC_TF32X3 && o.prec != TTM_PREC_BF16X3)
+    return set_err(TTM_ERR_INVALID_ARG, "unknown precision mode");
+  if (o.chi_out > 0 && (o.chi_max == 0 || o.chi_out < o.chi_max))
+    return set_err(TTM_ERR_UNSUPPORTED, "chi_out below chi_max (final rounding) is not built yet");
+  return TTM_OK;
+}
+
+static ttm_options default_options() {
+  ttm_options o;
+  std::memset(&o, 0, sizeof(o));
+  o.prec = TTM_PREC_FP64;
+  return o;
+}
+
+static ttm_status multiply_impl(ttm_handle* h, int32_t n, const ttm_tt* A, const ttm_tt* B, ttm_tt* out,
+                                ttm_report* rep) {
+  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 1 || !A || !B || !out) return set_err(TTM_ERR_INVALID_ARG, "null argument or n < 1");
+  ttm_status s = check_opts(h->s.opt);
+  if (s != TTM_OK) return s;
+  for (int i = 0; i < n; ++i) {
+    if ((s = check_tt(&A[i], "A", true)) != TTM_OK) return s;
+    if ((s = check_tt(&B[i], "B", true)) != TTM_OK) return s;
+    if (A[i].L != B[i].L || A[i].d != B[i].d) return set_err(TTM_ERR_SHAPE, "A and B differ in L or d");
+    if (A[i].L != A[0].L || A[i].d != A[0].d) return set_err(TTM_ERR_SHAPE, "batch items differ in L or d");
+    if (!out[i].bonds || !out[i].cores) return set_err(TTM_ERR_INVALID_ARG, "out bonds/cores arrays are NULL");
+  }
+  try {
+    TTM_CUDA(cudaSetDevice(h->s.device));
+    Engine e(h->s, n, A, B);
+    e.plan();
+    h->s.arena.ensure(e.bytes_needed());
+    std::vector<ttm_report> reps(n);
+    for (int i = 0; i < n; ++i) {
+      std::memset(&reps[i], 0, sizeof(ttm_report));
+      if (rep) {
+        reps[i].bond_trace = rep[i].bond_trace;
+        reps[i].bond_trace_len = rep[i].bond_trace_len;
+      }
+    }
+    e.execute(h->s.arena.ptr, h->s.opt, &reps, out);
+    if (rep)
+      for (int i = 0; i < n; ++i) rep[i] = reps[i];
+  } catch (const Error& err) {
+    return set_err(err.status, err.what());
+  } catch (const std::exception& ex) {
+    return set_err(TTM_ERR_INVALID_ARG, ex.what());
+  }
+  return TTM_OK;
+}
+
+}  // namespace ttm
+
+using namespace ttm;
+
+extern "C" {
+
+ttm_status ttm_create(ttm_handle** h, int device, void* cuda_stream, const ttm_options* opt) {
+  if (!h) return set_err(TTM_ERR_INVALID_ARG, "h is NULL");
+  *h = nullptr;
+  ttm_options o = opt ? *opt : default_options();
+  ttm_status s = check_opts(o);
+  if (s != TTM_OK) return s;
+  ttm_handle* H = new (std::nothrow) ttm_handle();
+  if (!H) return set_err(TTM_ERR_NOMEM, "host allocation failed");
+  try {
+    TTM_CUDA(cudaSetDevice(device));
+    H->s.device = device;
+    H->s.stream = (cudaStream_t)cuda_stream;
+    H->s.opt = o;
+    TTM_CUDA(cudaDeviceGetAttribute(&H->s.num_sms, cudaDevAttrMultiProcessorCount, device));
+    TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&H->s.coop_hest, hestenes_kernel<double>, 256, 0));
+    TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&H->s.coop_hest32, hestenes_kernel<float>, 256, 0));
+    TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&H->s.coop_qr, householder_kernel, 256, 0));
+    int coop = 0;
+    TTM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+    if (!coop) throw Error(TTM_ERR_UNSUPPORTED, "device lacks cooperative launch");
+    TTM_CUDA(cudaEventCreate(&H->s.ev0));
+    TTM_CUDA(cudaEventCreate(&H->s.ev1));
+  } catch (const Error& err) {
+    delete H;
+    return set_err(err.status, err.what());
+  }
+  *h = H;
+  return TTM_OK;
+}
+
+ttm_status ttm_destroy(ttm_handle* h) {
+  if (!h) return TTM_OK;
+  cudaSetDevice(h->s.device);
+  if (h->s.stream) cudaStreamSynchronize(h->s.stream);
+  else cudaDeviceSynchronize();
+  if (h->s.ev0) cudaEventDestroy(h->s.ev0);
+  if (h->s.ev1) cudaEventDestroy(h->s.ev1);
+  delete h;
+  return TTM_OK;
+}
+
+ttm_status ttm_set_options(ttm_handle* h, const ttm_options* opt) {
+  if (!h || !opt) return set_err(TTM_ERR_INVALID_ARG, "null argument");
+  ttm_status s = check_opts(*opt);
+  if (s != TTM_OK) return s;
+  h->s.opt = *opt;
+  return TTM_OK;
+}
+
+ttm_status ttm_multiply(ttm_handle* h, const ttm_tt* A, const ttm_tt* B, ttm_tt* out, ttm_report* rep) {
+  return multiply_impl(h, 1, A, B, out, rep);
+}
+
+ttm_status ttm_multiply_batched(ttm_handle* h, int32_t n, const ttm_tt* A, const ttm_tt* B, ttm_tt* out,
+                                ttm_report* rep) {
+  return multiply_impl(h, n, A, B, out, rep);
+}
+
+int64_t ttm_output_capacity(const ttm_tt* A, const ttm_tt* B, const ttm_options* opt) {
+  if (check_tt(A, "A", false) != TTM_OK || check_tt(B, "B", false) != TTM_OK) return -1;
+  if (A->L != B->L || A->d != B->d) return -1;
+  ttm_options o = opt ? *opt : default_options();
+  try {
+    HandleState hs;
+    hs.opt = o;
+    Engine e(hs, 1, A, B);
+    e.plan();
+    return e.max_carriage();
+  } catch (...) {
+    return -1;
+  }
+}
+
+ttm_status ttm_backward(ttm_handle* h, ttm_loss, const ttm_tt*, const ttm_tt*, const ttm_tt*, double*,
+                        ttm_tt*, ttm_tt*) {
+  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
+  return set_err(TTM_ERR_UNSUPPORTED, "ttm_backward is not built yet");
+}
+
+ttm_status ttm_inner(ttm_handle* h, const ttm_tt*, const ttm_tt*, double*) {
+  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
+  return set_err(TTM_ERR_UNSUPPORTED, "ttm_inner is not built yet");
+}
+
+ttm_status ttm_inner3(ttm_handle* h, const ttm_tt*, const ttm_tt*, const ttm_tt*, double*) {
+  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
+  return set_err(TTM_ERR_UNSUPPORTED, "ttm_inner3 is not built yet");
+}
+
+ttm_status ttm_synchronize(ttm_handle* h) {
+  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
+  cudaError_t e = h->s.stream ? cudaStreamSynchronize(h->s.stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_err(TTM_ERR_CUDA, cudaGetErrorString(e));
+  return TTM_OK;
+}
+
+ttm_status ttm_tt_free(ttm_handle* h, ttm_tt* t) {
+  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
+  if (t && !t->on_host && t->cores)
+    for (int k = 0; k < t->L; ++k) t->cores[k] = nullptr;
+  return TTM_OK;
+}
+
+const char* ttm_last_error(void) { return g_last_error.c_str(); }
+
+const char* ttm_version(void) { return "ttm-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+// ttm_common.cuh -- shared device-side data model of the TTM engine.
+//
+// Every product of a batch owns a row of three tables in device memory:
+//   buf  [z][nb]   : pointers to its carriage buffers and workspaces,
+//   bond [z][nbd]  : the current value of every bond id (written by the kernels
+//                    that create bonds: QR moves, Swap truncations),
+//   stat [z][ns]   : float64 statistics (discarded weights, norms, flop counters),
+//   istat[z][nis]  : int32 statistics (max bond, Jacobi sweeps, status flags).
+// The host walks a static schedule and passes only ids; the kernels read the
+// realised bond values, so the whole sweep needs no host synchronisation and can
+// be captured in a CUDA graph. Grids are sized by host-side upper bounds and
+// blocks beyond the realised sizes exit early. gridDim.z (or a loop) runs over
+// the products of a batch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttm {
+
+struct Tables {
+  double** buf;
+  int* bond;
+  double* stat;
+  int* istat;
+  int nb, nbd, ns, nis;
+  int nz;  // products in this launch
+};
+
+__device__ __forceinline__ int bondv(const Tables& t, int z, int id) {
+  return id < 0 ? 1 : t.bond[z * t.nbd + id];
+}
+__device__ __forceinline__ double* bufp(const Tables& t, int z, int id) {
+  return t.buf[z * t.nb + id];
+}
+
+// istat slots
+enum { IS_STATUS = 0, IS_MAX_BOND = 1, IS_SWEEPS_MAX = 2, IS_NONCONV = 3, IS_NFIXED = 4 };
+// stat slots (the per-truncation weights follow from ST_W0)
+enum { ST_WSUM = 0, ST_WSQRT = 1, ST_JFLOPS = 2, ST_JFLOPS32 = 3, ST_NFIXED = 4 };
+
+// A dimension written as mul * bond[id] (id < 0 means the constant mul).
+struct Dim {
+  int mul, id;
+  __device__ __forceinline__ int eval(const Tables& t, int z) const { return mul * bondv(t, z, id); }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace ttm

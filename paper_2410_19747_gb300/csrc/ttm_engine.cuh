@@ -1,0 +1,250 @@
+// ttm_engine.cuh -- host side of the sweep: plans the static schedule of Sec. II.B
+// (Eq. tensor, Contract, Swap, QR gauge moves) once with upper bounds on every bond,
+// then walks it again launching the kernels. Both walks run the same code
+// (Engine::run), so ids and buffers agree by construction.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "ttm.h"
+#include "ttm_common.cuh"
+#include "ttm_copy.cuh"
+#include "ttm_gemm.cuh"
+#include "ttm_qr.cuh"
+#include "ttm_svd.cuh"
+
+namespace ttm {
+
+struct Error : std::runtime_error {
+  ttm_status status;
+  Error(ttm_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define TTM_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::ttm::Error(TTM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + \
+                                           " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+  } while (0)
+
+constexpr int kMaxBond = 8192;      // largest bond the planner accepts
+constexpr int kDefaultSweeps = 40;  // one-sided Jacobi sweep limit
+
+struct DeviceArena {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t need) {
+    if (need <= bytes) return;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(TTM_ERR_NOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
+    }
+    bytes = need;
+  }
+  ~DeviceArena() {
+    if (ptr) cudaFree(ptr);
+  }
+};
+
+// Per-handle state.
+struct HandleState {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ttm_options opt{};
+  int num_sms = 0;
+  int coop_hest = 0, coop_hest32 = 0, coop_qr = 0;  // co-resident blocks per SM (cooperative kernels)
+  DeviceArena arena;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> prof_events;  // pairs around Jacobi launches (profile_kernels)
+  ~HandleState() {
+    for (cudaEvent_t e : prof_events) cudaEventDestroy(e);
+  }
+};
+
+enum StepKind { SK_QR = 0, SK_SWAP = 1, SK_CONTRACT = 2 };
+struct StepLog {
+  int kind;
+  int b0, b1, b2, b3;  // bond ids (meaning per kind)
+};
+
+class Engine {
+ public:
+  Engine(HandleState& hs, int Z, const ttm_tt* A, const ttm_tt* B)
+      : hs_(hs), Z_(Z), A_(A), B_(B), L_(A[0].L), d_(A[0].d), opt_(hs.opt) {}
+
+  // ------------------------------------------------------------------ planning
+  void plan() {
+    launch_ = false;
+    reset_ids();
+    run();
+    // sizes
+    nchain_ = (int)nbuf_total_;
+    nb_ = nchain_ + WS_COUNT;
+  }
+
+  size_t bytes_needed() const { return per_product_bytes() * Z_ + table_bytes(); }
+
+  // ------------------------------------------------------------------ execution
+  void execute(void* arena, const ttm_options& opt, std::vector<ttm_report>* reps, ttm_tt* outs);
+
+  int L() const { return L_; }
+  int d() const { return d_; }
+  long max_carriage() const { return carriage_elems_; }
+
+ private:
+  enum { WS_T = 0, WS_V, WS_NRM, WS_SORT, WS_PERM, WS_TAU, WS_R, WS_Q, WS_W32, WS_V32, WS_X, WS_COUNT };
+
+  HandleState& hs_;
+  int Z_;
+  const ttm_tt* A_;
+  const ttm_tt* B_;
+  int L_, d_;
+  ttm_options opt_{};
+  bool launch_ = false;
+  // ids
+  std::vector<std::vector<int>> ub_;  // ub_[id][z]
+  std::vector<std::vector<int>> exact_;  // exact host values for input bonds, else empty
+  std::vector<int> free_bufs_;
+  long nbuf_total_ = 0;
+  int nchain_ = 0, nb_ = 0;
+  int n_trunc_ = 0;
+  std::vector<StepLog> log_;
+  std::vector<std::vector<int>> trace_ids_;  // chain bond ids after each Contract
+  std::vector<int> out_buf_, out_bond_;      // output carriages and their bonds
+  // sizes (elements, per product)
+  long carriage_elems_ = 1, t_elems_ = 1, v_elems_ = 1, vec_elems_ = 1, r_elems_ = 1, q_elems_ = 1;
+  long x_elems_ = 1;  // float64 elements of the X workspace (max(m, n) * n)
+  // device tables (launch pass)
+  Tables tab_{};
+  int* counters_ = nullptr;
+  double* fro2_ = nullptr;
+  int counter_stride_ = 0;  // ints per Jacobi launch
+  int jac_launch_ = 0;
+  int* d_bond_ = nullptr;
+  double** d_buf_ = nullptr;
+  double* d_stat_ = nullptr;
+  int* d_istat_ = nullptr;
+  std::vector<double*> hbuf_;  // host copy of the buffer table
+
+  void reset_ids() {
+    ub_.clear();
+    exact_.clear();
+    free_bufs_.clear();
+    nbuf_total_ = 0;
+    n_trunc_ = 0;
+    log_.clear();
+    trace_ids_.clear();
+    jac_launch_ = 0;
+  }
+
+  int umax(int id) const {
+    int m = 1;
+    for (int v : ub_[id]) m = std::max(m, v);
+    return m;
+  }
+  int new_bond(const std::vector<int>& ub, const std::vector<int>* exact = nullptr) {
+    for (int v : ub)
+      if (v > kMaxBond)
+        throw Error(TTM_ERR_RANK_CAP, "a bond upper bound reaches " + std::to_string(v) +
+                                          " (> " + std::to_string(kMaxBond) + "); set chi_max");
+    ub_.push_back(ub);
+    exact_.push_back(exact ? *exact : std::vector<int>());
+    return (int)ub_.size() - 1;
+  }
+  int get_buf() {
+    if (!free_bufs_.empty()) {
+      int b = free_bufs_.back();
+      free_bufs_.pop_back();
+      return b;
+    }
+    return (int)nbuf_total_++;
+  }
+  void put_buf(int b) { free_bufs_.push_back(b); }
+  void note_carriage(int il, int ir) {
+    for (int z = 0; z < Z_; ++z)
+      carriage_elems_ = std::max(carriage_elems_, (long)ub_[il][z] * d_ * ub_[ir][z]);
+  }
+  int ws(int w) const { return nchain_ + w; }
+
+  size_t per_product_bytes() const {
+    long e = (long)nchain_ * carriage_elems_ + t_elems_ + v_elems_ + 3 * vec_elems_ + vec_elems_ +
+             r_elems_ + q_elems_ + (t_elems_ / 2 + 1) + (v_elems_ / 2 + 1) + x_elems_;
+    // every buffer aligned to 256 bytes
+    return (size_t)e * 8 + (size_t)(nb_ + 1) * 256;
+  }
+  size_t table_bytes() const {
+    size_t b = 0;
+    b += (size_t)Z_ * nb_ * sizeof(double*) + 256;
+    b += (size_t)Z_ * ub_.size() * sizeof(int) + 256;
+    b += (size_t)Z_ * (ST_NFIXED + n_trunc_) * sizeof(double) + 256;
+    b += (size_t)Z_ * IS_NFIXED * sizeof(int) + 256;
+    b += (size_t)std::max(1, jac_launch_) * Z_ * max_sweeps() * sizeof(int) + 256;
+    b += (size_t)std::max(1, jac_launch_) * Z_ * sizeof(double) + 256;
+    return b;
+  }
+  int max_sweeps() const { return opt_.max_sweeps > 0 ? opt_.max_sweeps : kDefaultSweeps; }
+
+  // grid helpers
+  static unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
+  template <class F>
+  void gemm(const F& f, int nbatch, int M_ub, int N_ub) {
+    if (!launch_) return;
+    dim3 grid(cdiv(N_ub, GT), cdiv(M_ub, GT), (unsigned)(Z_ * nbatch));
+    dgemm_kernel<F><<<grid, 256, 0, hs_.stream>>>(f, nbatch);
+    TTM_CUDA(cudaGetLastError());
+    ++launches_;
+  }
+  template <class F>
+  void copy2d(const F& f, int nbatch, int R_ub, int C_ub) {
+    if (!launch_) return;
+    dim3 grid(cdiv(C_ub, 32), cdiv(R_ub, 32), (unsigned)(Z_ * nbatch));
+    copy2d_kernel<F><<<grid, 256, 0, hs_.stream>>>(f, nbatch);
+    TTM_CUDA(cudaGetLastError());
+    ++launches_;
+  }
+  void cast(int src, int dst, Dim rows, Dim cols, int to_float, long n_ub) {
+    if (!launch_) return;
+    CastArgs ca{tab_, src, dst, rows, cols, to_float};
+    dim3 g((unsigned)std::min<long>(1024, cdiv(n_ub, 256)), Z_);
+    cast_kernel<<<g, 256, 0, hs_.stream>>>(ca);
+    TTM_CUDA(cudaGetLastError());
+    ++launches_;
+  }
+  // Cooperative launch of 256-thread CTAs with one warp per work item (`units` items per round).
+  void coop(void* fn, void* args, int blocks_per_sm, long units, int units_per_cta = 8) {
+    long blocks = std::max(1L, std::min((long)blocks_per_sm * hs_.num_sms, (units + units_per_cta - 1) / units_per_cta));
+    void* kargs[] = {args};
+    TTM_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), kargs, 0, hs_.stream));
+    ++launches_;
+  }
+  long launches_ = 0;
+  int prof_used_ = 0;
+  cudaEvent_t prof_event() {
+    if (prof_used_ >= (int)hs_.prof_events.size()) {
+      cudaEvent_t e;
+      TTM_CUDA(cudaEventCreate(&e));
+      hs_.prof_events.push_back(e);
+    }
+    return hs_.prof_events[prof_used_++];
+  }
+
+  // ------------------------------------------------------------------ steps
+  void load_core(const ttm_tt* T, int k, int buf);
+  void qr_move(int c, int& nx, int bl, int& br, int brr);
+  int swap(int x, int y, int bl, int bm, int br);
+  void order_and_truncate(Dim m, Dim n, int ibond, int record, int wslot, int n_ub, int ieps = -1);
+  void contract(int kb, int mb, int out, int il, int ia, int ir);
+  void run();
+};
+
+}  // namespace ttm

@@ -1,0 +1,60 @@
+"""CPU checks of the C ABI boundary: the library builds, loads without a GPU, and exports
+every function include/ttm.h declares. No compute call is made here."""
+
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "ttm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(ttm_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import paper_2410_19747_gb300 as pkg
+    pkg.build()
+    return pkg.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ["ttm_create", "ttm_destroy", "ttm_multiply", "ttm_multiply_batched", "ttm_backward"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_2410_19747_gb300 as pkg
+    names = _declared_functions()
+    assert sorted(names) == sorted(pkg.EXPORTED)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.ttm_version().decode().startswith("ttm-gb300")
+
+
+def test_invalid_arguments_are_rejected_without_gpu(lib):
+    import ctypes
+    import paper_2410_19747_gb300.binding as b
+    # NULL handle and NULL descriptors are rejected before any CUDA call
+    assert lib.ttm_multiply(None, None, None, None, None) == -1
+    assert lib.ttm_create(None, 0, None, None) == -1
+    o = b.make_options(eps=1.5)
+    h = ctypes.c_void_p()
+    assert lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == -1
+    assert b"eps" in lib.ttm_last_error()
+    # shape validation in ttm_output_capacity (host-only planning)
+    import numpy as np
+    A = [np.zeros((1, 2, 2)), np.zeros((2, 2, 1))]
+    B = [np.zeros((1, 2, 2)), np.zeros((2, 2, 1))]
+    assert b.output_capacity(A, B) == 2 * 2 * 2 or b.output_capacity(A, B) > 0
+    bad = [np.zeros((1, 2, 3)), np.zeros((3, 2, 1))]   # bond 3 > min(2^1, 2^1)
+    assert b.output_capacity(bad, B) == -1

@@ -30,7 +30,7 @@ def _left_sweep(cores):
         Q, R = np.linalg.qr(C[k].reshape(Dl * d, Dr))
         C[k] = Q.reshape(Dl, d, Q.shape[1])
         C[k + 1] = np.tensordot(R, C[k + 1], axes=(1, 0))
-    return C
+    return [np.ascontiguousarray(c) for c in C]
 
 
 def _right_sweep(cores):
@@ -38,9 +38,9 @@ def _right_sweep(cores):
     for k in range(len(C) - 1, 0, -1):
         Dl, d, Dr = C[k].shape
         Q, R = np.linalg.qr(C[k].reshape(Dl, d * Dr).T)
-        C[k] = Q.T.reshape(Q.shape[1], d, Dr)
+        C[k] = np.ascontiguousarray(Q.T.reshape(Q.shape[1], d, Dr))
         C[k - 1] = np.tensordot(C[k - 1], R.T, axes=(2, 0))
-    return C
+    return [np.ascontiguousarray(c) for c in C]
 
 
 def rand_tt(L, d, chi, seed, canon=None, scale=1.0):
@@ -80,7 +80,9 @@ def rand_tt_spectral(L, d, chi, seed, decay=1.0):
             sig /= np.linalg.norm(sig)
             core = sig[:, None, None] * core
         cores.append(core)
-    return _right_sweep(cores)
+    C = _right_sweep(cores)
+    C[0] = C[0] / np.linalg.norm(C[0])   # right-canonical: the norm sits in core 1
+    return C
 
 
 def qtt_trig(L, omega, phase=0.0, kind="cos"):
