@@ -159,8 +159,7 @@ def model_flops(L, d, chi):
     # sweep: iteration i moves the centre through Pi_{i+1}..Pi_N and swaps back
     for i in range(L - 1, 0, -1):
         for j in range(i + 1, L + 1):
-            D = min(chi, ub(j, L) ** 2) if False else chi
-            fl += qr(d * D, D, D, D)
+            fl += qr(d * chi, chi, chi, chi)
         for j in range(L, i, -1):
             Dl = Dm = Dr = chi
             m = n = d * chi
