@@ -249,16 +249,19 @@ def main():
     value = products / t
 
     # end to end through the public call from pinned host buffers
-    Ah = [torch.from_numpy(c).pin_memory() for c in A]
-    Bh = [torch.from_numpy(c).pin_memory() for c in B]
-    e2e_t, h2d, d2h = 0.0, 0, 0
-    for _ in range(args.e2e_steps):
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        outh, rh = pkg.ttm_multiply(h, Ah, Bh, **kw)
-        e2e_t += time.perf_counter() - t0
-        h2d = sum(c.numel() * 8 for c in Ah) + sum(c.numel() * 8 for c in Bh)
-        d2h = sum(c.size * 8 for c in outh)
+    e2e_t, h2d, d2h, e2e_err = 0.0, 0, 0, None
+    try:
+        Ah = [torch.from_numpy(c).pin_memory() for c in A]
+        Bh = [torch.from_numpy(c).pin_memory() for c in B]
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            outh, rh = pkg.ttm_multiply(h, Ah, Bh, **kw)
+            e2e_t += time.perf_counter() - t0
+            h2d = sum(int(c.numel()) * 8 for c in Ah) + sum(int(c.numel()) * 8 for c in Bh)
+            d2h = sum(int(c.numel()) * 8 for c in outh)
+    except Exception as ex:  # the device-resident number above stays valid
+        e2e_err = repr(ex)
     e2e_val = world * args.e2e_steps / e2e_t if e2e_t > 0 else None
     if dist:
         ev = torch.tensor([e2e_t], device=dev)
@@ -284,7 +287,8 @@ def main():
                          "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
                          "share_of_step": jac_ms / 1e3 / t_local if t_local > 0 else None,
                          "launches": jac_launch, "avg_launch_ms": jac_ms / max(1, jac_launch)},
-            "e2e": {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    **({"error": e2e_err} if e2e_err else {})},
             "gpu_launches": int(sum(r["n_kernel_launches"] for r in reps)),
             "clocks": clk.summary(),
             "report": {k: r0[k] for k in ("n_swaps", "n_contracts", "n_qr", "max_bond", "discarded_weight",

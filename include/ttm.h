@@ -37,8 +37,8 @@ typedef struct ttm_handle ttm_handle;
 typedef enum {
   TTM_OK = 0,
   TTM_ERR_INVALID_ARG = -1, /* null pointer, eps outside [0,1), L < 1, d < 2 ...      */
-  TTM_ERR_SHAPE = -2,       /* boundary bond != 1, bond above min(d^i, d^(L-i)), A/B
-                               mismatch, caller buffer too small                     */
+  TTM_ERR_SHAPE = -2,       /* boundary bond != 1, bond < 1, A/B mismatch, caller
+                               buffer too small                                      */
   TTM_ERR_NOMEM = -3,       /* device allocation failed                              */
   TTM_ERR_WORKSPACE = -4,   /* a caller-sized workspace is too small                 */
   TTM_ERR_NONFINITE = -5,   /* NaN/Inf met in an input (only when checked)           */
@@ -51,9 +51,13 @@ typedef enum {
 /* Arithmetic of the GEMM-shaped contractions. Decompositions (QR, SVD) and norms
  * always run in float64 on the GPU. */
 typedef enum {
-  TTM_PREC_FP64 = 0,    /* plain float64 everywhere (the reference form)             */
-  TTM_PREC_TF32X3 = 1,  /* tensor-core split products, float32 accumulation per tile */
-  TTM_PREC_BF16X3 = 2   /* tensor-core bf16 split products                            */
+  TTM_PREC_FP64 = 0,       /* plain float64 everywhere (the reference form): the Swap SVD
+                              is polished in float64 until its one-sided Jacobi converges */
+  TTM_PREC_TF32X3 = 1,     /* tensor-core split products: not built (TTM_ERR_UNSUPPORTED) */
+  TTM_PREC_BF16X3 = 2,     /* tensor-core split products: not built (TTM_ERR_UNSUPPORTED) */
+  TTM_PREC_MIXED_F32 = 3   /* the SVD rotation is found in float32 and polished by at most
+                              max_sweeps (default 3) float64 sweeps; the factorisation
+                              W V^T = Theta, the GEMMs, QR and norms stay float64          */
 } ttm_precision;
 
 typedef enum {

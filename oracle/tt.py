@@ -145,7 +145,14 @@ def inner3(W, A, B):
     """
     E = np.ones((1, 1, 1))
     for Wk, Ak, Bk in zip(W, A, B):
-        E = np.einsum('xab,xsw,asc,bsd->wcd', E, Wk, Ak, Bk, optimize=True)
+        d = Wk.shape[1]
+        # contract the B layer, then the A layer on the same s, then the W layer on the same s
+        T1 = np.tensordot(E, Bk, axes=(2, 0))                     # [x, a, s, d]
+        En = np.zeros((Wk.shape[2], Ak.shape[2], Bk.shape[2]))
+        for s in range(d):
+            T2 = np.tensordot(Ak[:, s, :], T1[:, :, s, :], axes=(0, 1))   # [c, x, d]
+            En += np.tensordot(Wk[:, s, :], T2, axes=(0, 1))               # [w, c, d]
+        E = En
     return float(E[0, 0, 0])
 
 

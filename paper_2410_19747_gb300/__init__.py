@@ -11,3 +11,4 @@ from .binding import (  # noqa: F401
     ttm_backward, ttm_inner, ttm_inner3, ttm_multiply, ttm_multiply_batched,
 )
 from ._build import build  # noqa: F401
+from .autograd import TTMProductLoss, product_loss  # noqa: F401

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libttm.so")
-SOURCES = ["ttm_api.cu"]
+SOURCES = ["ttm_api.cu", "ttm_env.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,7 +14,7 @@ import numpy as np
 from . import _build
 
 TTM_OK = 0
-PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "mixed": 3}
 LOSS = {"inner": 0, "sqdist": 1}
 STATUS = {0: "TTM_OK", -1: "TTM_ERR_INVALID_ARG", -2: "TTM_ERR_SHAPE", -3: "TTM_ERR_NOMEM",
           -4: "TTM_ERR_WORKSPACE", -5: "TTM_ERR_NONFINITE", -6: "TTM_ERR_CUDA",

@@ -122,7 +122,9 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
         pe1 = prof_event();
         TTM_CUDA(cudaEventRecord(pe0, hs_.stream));
       }
-      HestArgs h64{tab_, ws(WS_X), ws(WS_V), m, n, npad_ub, max_sweeps(),
+      const int polish_sweeps =
+          opt_.prec == TTM_PREC_MIXED_F32 ? (opt_.max_sweeps > 0 ? opt_.max_sweeps : 3) : max_sweeps();
+      HestArgs h64{tab_, ws(WS_X), ws(WS_V), m, n, npad_ub, polish_sweeps,
                    counters_ + (size_t)sw64 * counter_stride_,
                    1e-10, 64 * 1.11e-16,
                    fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), -1};
@@ -428,12 +430,12 @@ static ttm_status check_tt(const ttm_tt* t, const char* name, bool need_cores) {
   if (need_cores && !t->cores) return set_err(TTM_ERR_INVALID_ARG, std::string(name) + ": cores is NULL");
   if (t->bonds[0] != 1 || t->bonds[t->L] != 1)
     return set_err(TTM_ERR_SHAPE, std::string(name) + ": boundary bonds must be 1");
+  // Bonds above the unfolding bound min(d^i, d^(L-i)) are redundant but valid (a TTM output
+  // can carry them next to the ends of the train), so only positivity is required.
   for (int i = 0; i <= t->L; ++i) {
-    // bound min(d^i, d^(L-i)), saturating
-    double lim = std::min(std::pow((double)t->d, i), std::pow((double)t->d, t->L - i));
-    if (t->bonds[i] < 1 || (double)t->bonds[i] > lim)
+    if (t->bonds[i] < 1)
       return set_err(TTM_ERR_SHAPE, std::string(name) + ": bond " + std::to_string(i) + " = " +
-                                        std::to_string(t->bonds[i]) + " outside [1, min(d^i, d^(L-i))]");
+                                        std::to_string(t->bonds[i]) + " is below 1");
     if (t->bonds[i] > kMaxBond) return set_err(TTM_ERR_RANK_CAP, std::string(name) + ": bond too large");
   }
   if (need_cores)
@@ -445,8 +447,11 @@ static ttm_status check_tt(const ttm_tt* t, const char* name, bool need_cores) {
 static ttm_status check_opts(const ttm_options& o) {
   if (!(o.eps >= 0.0 && o.eps < 1.0)) return set_err(TTM_ERR_INVALID_ARG, "eps must lie in [0, 1)");
   if (o.chi_max < 0 || o.chi_out < 0) return set_err(TTM_ERR_INVALID_ARG, "negative cap");
-  if (o.prec != TTM_PREC_FP64 && o.prec != TTM_PREC_TF32X3 && o.prec != TTM_PREC_BF16X3)
+  if (o.prec != TTM_PREC_FP64 && o.prec != TTM_PREC_TF32X3 && o.prec != TTM_PREC_BF16X3 &&
+      o.prec != TTM_PREC_MIXED_F32)
     return set_err(TTM_ERR_INVALID_ARG, "unknown precision mode");
+  if (o.prec == TTM_PREC_TF32X3 || o.prec == TTM_PREC_BF16X3)
+    return set_err(TTM_ERR_UNSUPPORTED, "tensor-core split precision modes are not built");
   if (o.chi_out > 0 && (o.chi_max == 0 || o.chi_out < o.chi_max))
     return set_err(TTM_ERR_UNSUPPORTED, "chi_out below chi_max (final rounding) is not built yet");
   return TTM_OK;
@@ -575,20 +580,66 @@ int64_t ttm_output_capacity(const ttm_tt* A, const ttm_tt* B, const ttm_options*
   }
 }
 
-ttm_status ttm_backward(ttm_handle* h, ttm_loss, const ttm_tt*, const ttm_tt*, const ttm_tt*, double*,
-                        ttm_tt*, ttm_tt*) {
-  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
-  return set_err(TTM_ERR_UNSUPPORTED, "ttm_backward is not built yet");
+static ttm_status check_env_tt(const ttm_tt* t, const char* name, int L, int d) {
+  ttm_status s = check_tt(t, name, true);
+  if (s != TTM_OK) return s;
+  if (t->on_host) return set_err(TTM_ERR_UNSUPPORTED, std::string(name) + ": environments take device cores");
+  if (t->L != L || t->d != d) return set_err(TTM_ERR_SHAPE, std::string(name) + ": L or d differs");
+  return TTM_OK;
 }
 
-ttm_status ttm_inner(ttm_handle* h, const ttm_tt*, const ttm_tt*, double*) {
-  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
-  return set_err(TTM_ERR_UNSUPPORTED, "ttm_inner is not built yet");
+ttm_status ttm_backward(ttm_handle* h, ttm_loss kind, const ttm_tt* A, const ttm_tt* B, const ttm_tt* WC,
+                        double* loss_out, ttm_tt* gradA, ttm_tt* gradB) {
+  if (!h || !A || !B || !WC || !loss_out) return set_err(TTM_ERR_INVALID_ARG, "null argument");
+  if (kind != TTM_LOSS_INNER && kind != TTM_LOSS_SQDIST) return set_err(TTM_ERR_INVALID_ARG, "unknown loss");
+  ttm_status s;
+  if ((s = check_env_tt(A, "A", A->L, A->d)) != TTM_OK) return s;
+  if ((s = check_env_tt(B, "B", A->L, A->d)) != TTM_OK) return s;
+  if ((s = check_env_tt(WC, "W_or_C", A->L, A->d)) != TTM_OK) return s;
+  for (ttm_tt* g : {gradA, gradB}) {
+    if (!g) continue;
+    const ttm_tt* ref = (g == gradA) ? A : B;
+    if ((s = check_env_tt(g, "grad", A->L, A->d)) != TTM_OK) return s;
+    for (int i = 0; i <= A->L; ++i)
+      if (g->bonds[i] != ref->bonds[i]) return set_err(TTM_ERR_SHAPE, "gradient bonds differ from the train's");
+  }
+  try {
+    TTM_CUDA(cudaSetDevice(h->s.device));
+    *loss_out = env_backward(h->s, h->s.env_arena, (int)kind, *A, *B, *WC, gradA, gradB);
+    TTM_CUDA(h->s.stream ? cudaStreamSynchronize(h->s.stream) : cudaDeviceSynchronize());
+  } catch (const Error& err) {
+    return set_err(err.status, err.what());
+  }
+  return TTM_OK;
 }
 
-ttm_status ttm_inner3(ttm_handle* h, const ttm_tt*, const ttm_tt*, const ttm_tt*, double*) {
-  if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
-  return set_err(TTM_ERR_UNSUPPORTED, "ttm_inner3 is not built yet");
+ttm_status ttm_inner(ttm_handle* h, const ttm_tt* X, const ttm_tt* Y, double* outv) {
+  if (!h || !X || !Y || !outv) return set_err(TTM_ERR_INVALID_ARG, "null argument");
+  ttm_status s;
+  if ((s = check_env_tt(X, "X", X->L, X->d)) != TTM_OK) return s;
+  if ((s = check_env_tt(Y, "Y", X->L, X->d)) != TTM_OK) return s;
+  try {
+    TTM_CUDA(cudaSetDevice(h->s.device));
+    *outv = env_inner(h->s, h->s.env_arena, *X, *Y);
+  } catch (const Error& err) {
+    return set_err(err.status, err.what());
+  }
+  return TTM_OK;
+}
+
+ttm_status ttm_inner3(ttm_handle* h, const ttm_tt* W, const ttm_tt* A, const ttm_tt* B, double* outv) {
+  if (!h || !W || !A || !B || !outv) return set_err(TTM_ERR_INVALID_ARG, "null argument");
+  ttm_status s;
+  if ((s = check_env_tt(W, "W", W->L, W->d)) != TTM_OK) return s;
+  if ((s = check_env_tt(A, "A", W->L, W->d)) != TTM_OK) return s;
+  if ((s = check_env_tt(B, "B", W->L, W->d)) != TTM_OK) return s;
+  try {
+    TTM_CUDA(cudaSetDevice(h->s.device));
+    *outv = env_inner3(h->s, h->s.env_arena, *W, *A, *B);
+  } catch (const Error& err) {
+    return set_err(err.status, err.what());
+  }
+  return TTM_OK;
 }
 
 ttm_status ttm_synchronize(ttm_handle* h) {

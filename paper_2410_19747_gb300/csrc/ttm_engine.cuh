@@ -13,63 +13,13 @@
 
 #include "ttm.h"
 #include "ttm_common.cuh"
+#include "ttm_host.hpp"
 #include "ttm_copy.cuh"
 #include "ttm_gemm.cuh"
 #include "ttm_qr.cuh"
 #include "ttm_svd.cuh"
 
 namespace ttm {
-
-struct Error : std::runtime_error {
-  ttm_status status;
-  Error(ttm_status s, const std::string& m) : std::runtime_error(m), status(s) {}
-};
-
-#define TTM_CUDA(call)                                                                    \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      throw ::ttm::Error(TTM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + \
-                                           " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
-  } while (0)
-
-constexpr int kMaxBond = 8192;      // largest bond the planner accepts
-constexpr int kDefaultSweeps = 40;  // one-sided Jacobi sweep limit
-
-struct DeviceArena {
-  void* ptr = nullptr;
-  size_t bytes = 0;
-  void ensure(size_t need) {
-    if (need <= bytes) return;
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    bytes = 0;
-    cudaError_t e = cudaMalloc(&ptr, need);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      throw Error(TTM_ERR_NOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
-    }
-    bytes = need;
-  }
-  ~DeviceArena() {
-    if (ptr) cudaFree(ptr);
-  }
-};
-
-// Per-handle state.
-struct HandleState {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  ttm_options opt{};
-  int num_sms = 0;
-  int coop_hest = 0, coop_hest32 = 0, coop_qr = 0;  // co-resident blocks per SM (cooperative kernels)
-  DeviceArena arena;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  std::vector<cudaEvent_t> prof_events;  // pairs around Jacobi launches (profile_kernels)
-  ~HandleState() {
-    for (cudaEvent_t e : prof_events) cudaEventDestroy(e);
-  }
-};
 
 enum StepKind { SK_QR = 0, SK_SWAP = 1, SK_CONTRACT = 2 };
 struct StepLog {

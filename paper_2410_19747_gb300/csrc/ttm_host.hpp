@@ -1,0 +1,75 @@
+// ttm_host.hpp -- host-side types shared by the translation units of libttm.so:
+// the internal exception carrying a ttm_status, the CUDA error check, the grow-only
+// device arena and the per-handle state.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "ttm.h"
+
+namespace ttm {
+
+struct Error : std::runtime_error {
+  ttm_status status;
+  Error(ttm_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define TTM_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::ttm::Error(TTM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + \
+                                           " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+  } while (0)
+
+constexpr int kMaxBond = 8192;      // largest bond the planner accepts
+constexpr int kDefaultSweeps = 40;  // one-sided Jacobi sweep limit
+
+struct DeviceArena {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t need) {
+    if (need <= bytes) return;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(TTM_ERR_NOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
+    }
+    bytes = need;
+  }
+  ~DeviceArena() {
+    if (ptr) cudaFree(ptr);
+  }
+};
+
+// Per-handle state.
+struct HandleState {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ttm_options opt{};
+  int num_sms = 0;
+  int coop_hest = 0, coop_hest32 = 0, coop_qr = 0;  // co-resident blocks per SM (cooperative kernels)
+  DeviceArena arena;      // sweep buffers and workspaces
+  DeviceArena env_arena;  // environments of ttm_inner / ttm_inner3 / ttm_backward
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> prof_events;  // pairs around Jacobi launches (profile_kernels)
+  ~HandleState() {
+    for (cudaEvent_t e : prof_events) cudaEventDestroy(e);
+  }
+};
+
+
+// Environment drivers (ttm_env.cu).
+double env_inner(HandleState& hs, DeviceArena& ar, const ttm_tt& X, const ttm_tt& Y);
+double env_inner3(HandleState& hs, DeviceArena& ar, const ttm_tt& W, const ttm_tt& A, const ttm_tt& B);
+double env_backward(HandleState& hs, DeviceArena& ar, int kind, const ttm_tt& A, const ttm_tt& B,
+                    const ttm_tt& WC, const ttm_tt* gA, const ttm_tt* gB);
+
+}  // namespace ttm

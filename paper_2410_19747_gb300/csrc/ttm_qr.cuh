@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(256) householder_kernel(QRArgs a) {
   const int lane = threadIdx.x & 31;
   const long gthread = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nthreads = (long)gridDim.x * blockDim.x;
-  const long gwarp = gthread >> 5, nwarps = nthreads >> 5;
+  // consecutive work items on different SMs (see the Jacobi kernel)
+  const long gwarp = (long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = nthreads >> 5;
   const int nz = a.t.nz;
 
   for (long z = gwarp; z < nz; z += nwarps) {

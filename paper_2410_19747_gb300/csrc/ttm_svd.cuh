@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
   const int lane = threadIdx.x & 31;
   const long gthread = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nthreads = (long)gridDim.x * blockDim.x;
-  const long gwarp = gthread >> 5, nwarps = nthreads >> 5;
+  // Work item i goes to warp (i mod gridDim.x) of CTA ..., i.e. consecutive items land on
+  // different SMs, so a round with fewer items than warps still uses every SM.
+  const long gwarp = (long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = nthreads >> 5;
   const int nz = a.t.nz;
 
   for (int z = 0; z < nz; ++z) {

@@ -56,5 +56,5 @@ def test_invalid_arguments_are_rejected_without_gpu(lib):
     A = [np.zeros((1, 2, 2)), np.zeros((2, 2, 1))]
     B = [np.zeros((1, 2, 2)), np.zeros((2, 2, 1))]
     assert b.output_capacity(A, B) == 2 * 2 * 2 or b.output_capacity(A, B) > 0
-    bad = [np.zeros((1, 2, 3)), np.zeros((3, 2, 1))]   # bond 3 > min(2^1, 2^1)
+    bad = [np.zeros((2, 2, 3)), np.zeros((3, 2, 1))]   # boundary bond 2 != 1
     assert b.output_capacity(bad, B) == -1
