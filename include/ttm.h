@@ -166,6 +166,34 @@ ttm_status ttm_inner(ttm_handle *h, const ttm_tt *X, const ttm_tt *Y, double *ou
 ttm_status ttm_inner3(ttm_handle *h, const ttm_tt *W, const ttm_tt *A, const ttm_tt *B,
                       double *out);
 
+/*
+ * Allocation-free product (no counterpart in the paper; an addition for callers that
+ * cannot allocate device memory). Some callers must not call cudaMalloc once they are
+ * running: a host application or plugin that reserves its device memory up front and
+ * forbids the heap from growing afterwards, code that runs when device memory is already
+ * exhausted, or a caller for which the implicit device-wide synchronisation of
+ * cudaMalloc/cudaFree is not acceptable. This entry point computes the same product as
+ * ttm_multiply for small trains without any device allocation: all workspace lives in a
+ * fixed device array of TTM_NOALLOC_SCRATCH_BYTES bytes that the library defines at file
+ * scope (every GPU that loads the library holds it until the process exits).
+ *   - A, B: device cores (on_host = 0). out: out->cores[k] must be caller device buffers
+ *     of at least ttm_output_capacity(...) doubles each; out->bonds receives the bonds.
+ *   - opt may be NULL (defaults as in ttm_create); profile_kernels is ignored.
+ *   - cuda_stream: the stream to run on (NULL = legacy default stream). The call blocks
+ *     until the result is in `out`.
+ *   - A product whose workspace exceeds TTM_NOALLOC_SCRATCH_BYTES is rejected with
+ *     TTM_ERR_WORKSPACE before any work is queued.
+ *   - The first call on a device (made current by the caller) looks up the device address
+ *     of the array; make that first call before any stream capture.
+ *   - Every call on a device uses the same array and leaves its contents behind (each call
+ *     re-initialises what it reads). Calls whose GPU work overlaps in time on one device
+ *     (different streams or host threads) race on the array: serialise them.
+ * No cudaMalloc, cudaFree or other allocating routine is called on this path.
+ */
+#define TTM_NOALLOC_SCRATCH_BYTES (16u << 20)
+ttm_status ttm_multiply_noalloc(const ttm_tt *A, const ttm_tt *B, ttm_tt *out, const ttm_options *opt,
+                                void *cuda_stream);
+
 /* Waits for all work queued on the handle's stream. */
 ttm_status ttm_synchronize(ttm_handle *h);
 /* Releases the handle-owned output of the last multiply (optional; ttm_destroy frees all). */

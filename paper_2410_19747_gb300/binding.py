@@ -23,7 +23,7 @@ STATUS = {0: "TTM_OK", -1: "TTM_ERR_INVALID_ARG", -2: "TTM_ERR_SHAPE", -3: "TTM_
 # Every symbol include/ttm.h declares (checked by the CPU test suite).
 EXPORTED = ["ttm_create", "ttm_destroy", "ttm_set_options", "ttm_multiply", "ttm_multiply_batched",
             "ttm_output_capacity", "ttm_backward", "ttm_inner", "ttm_inner3", "ttm_synchronize",
-            "ttm_tt_free", "ttm_last_error", "ttm_version"]
+            "ttm_tt_free", "ttm_last_error", "ttm_version", "ttm_multiply_noalloc"]
 
 
 class TTMError(RuntimeError):
@@ -84,6 +84,8 @@ def load_library(build_if_missing=False):
                                  P(ctypes.c_double), P(c_tt), P(c_tt)]
     lib.ttm_inner.argtypes = [ctypes.c_void_p, P(c_tt), P(c_tt), P(ctypes.c_double)]
     lib.ttm_inner3.argtypes = [ctypes.c_void_p, P(c_tt), P(c_tt), P(c_tt), P(ctypes.c_double)]
+    lib.ttm_multiply_noalloc.argtypes = [P(c_tt), P(c_tt), P(c_tt), P(c_options), ctypes.c_void_p]
+    lib.ttm_multiply_noalloc.restype = ctypes.c_int
     lib.ttm_synchronize.argtypes = [ctypes.c_void_p]
     lib.ttm_tt_free.argtypes = [ctypes.c_void_p, P(c_tt)]
     lib.ttm_last_error.restype = ctypes.c_char_p

@@ -300,7 +300,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     if (!exact_[id].empty())
       for (int z = 0; z < Z_; ++z) hb[(size_t)z * nbd + id] = exact_[id][z];
   cudaStream_t st = hs_.stream;
-  TTM_CUDA(cudaEventRecord(hs_.ev0, st));
+  if (hs_.ev0) TTM_CUDA(cudaEventRecord(hs_.ev0, st));
   TTM_CUDA(cudaMemcpyAsync(d_buf_, hbuf_.data(), hbuf_.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   TTM_CUDA(cudaMemcpyAsync(d_bond_, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   TTM_CUDA(cudaMemsetAsync(d_stat_, 0, (size_t)Z_ * ns * sizeof(double), st));
@@ -319,7 +319,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   run();
   if ((int)nbuf_total_ != nchain_planned || jac_launch_ != jac_planned)
     throw Error(TTM_ERR_INVALID_ARG, "internal: plan and launch walks disagree");
-  TTM_CUDA(cudaEventRecord(hs_.ev1, st));
+  if (hs_.ev1) TTM_CUDA(cudaEventRecord(hs_.ev1, st));
 
   // results
   std::vector<int> bonds((size_t)Z_ * nbd);
@@ -330,7 +330,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   TTM_CUDA(cudaMemcpyAsync(istat.data(), d_istat_, istat.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
   TTM_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
-  TTM_CUDA(cudaEventElapsedTime(&ms, hs_.ev0, hs_.ev1));
+  if (hs_.ev0 && hs_.ev1) TTM_CUDA(cudaEventElapsedTime(&ms, hs_.ev0, hs_.ev1));
   double jac_ms = 0.0;
   for (int q = 0; q + 1 < prof_used_; q += 2) {
     float x = 0.f;
@@ -653,6 +653,84 @@ ttm_status ttm_tt_free(ttm_handle* h, ttm_tt* t) {
   if (!h) return set_err(TTM_ERR_INVALID_ARG, "handle is NULL");
   if (t && !t->on_host && t->cores)
     for (int k = 0; k < t->L; ++k) t->cores[k] = nullptr;
+  return TTM_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free product
+
+// Workspace of ttm_multiply_noalloc: a fixed array in device memory, defined at file scope.
+// Host code must not use the symbol as an address (on the host it names a stand-in);
+// the device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TTM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+struct NoAllocDevice {
+  bool ready = false;
+  void* scratch = nullptr;
+  int num_sms = 0, coop_hest = 0, coop_hest32 = 0, coop_qr = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+}  // namespace
+
+ttm_status ttm_multiply_noalloc(const ttm_tt* A, const ttm_tt* B, ttm_tt* out, const ttm_options* opt,
+                                void* cuda_stream) {
+  if (!A || !B || !out) return set_err(TTM_ERR_INVALID_ARG, "null argument");
+  ttm_options o = opt ? *opt : default_options();
+  o.profile_kernels = 0;
+  ttm_status s = check_opts(o);
+  if (s != TTM_OK) return s;
+  if ((s = check_tt(A, "A", true)) != TTM_OK) return s;
+  if ((s = check_tt(B, "B", true)) != TTM_OK) return s;
+  if (A->L != B->L || A->d != B->d) return set_err(TTM_ERR_SHAPE, "A and B differ in L or d");
+  if (A->on_host || B->on_host || out->on_host)
+    return set_err(TTM_ERR_UNSUPPORTED, "the allocation-free product takes device cores only");
+  if (!out->bonds || !out->cores) return set_err(TTM_ERR_INVALID_ARG, "out bonds/cores arrays are NULL");
+  for (int k = 0; k < A->L; ++k)
+    if (!out->cores[k]) return set_err(TTM_ERR_INVALID_ARG, "out->cores must be caller device buffers");
+  try {
+    int dev = 0;
+    TTM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error(TTM_ERR_UNSUPPORTED, "device index above 63");
+    NoAllocDevice info;
+    {
+      std::lock_guard<std::mutex> lock(g_noalloc_mu);
+      NoAllocDevice& nd = g_noalloc_dev[dev];
+      if (!nd.ready) {
+        void* p = nullptr;
+        TTM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        TTM_CUDA(cudaDeviceGetAttribute(&nd.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd.coop_hest, hestenes_kernel<double>, 256, 0));
+        TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd.coop_hest32, hestenes_kernel<float>, 256, 0));
+        TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd.coop_qr, householder_kernel, 256, 0));
+        nd.scratch = p;
+        nd.ready = true;
+      }
+      info = nd;
+    }
+    HandleState hs;  // no arena is ever allocated through it on this path, and no events
+    hs.device = dev;
+    hs.stream = (cudaStream_t)cuda_stream;
+    hs.opt = o;
+    hs.num_sms = info.num_sms;
+    hs.coop_hest = info.coop_hest;
+    hs.coop_hest32 = info.coop_hest32;
+    hs.coop_qr = info.coop_qr;
+    Engine e(hs, 1, A, B);
+    e.plan();
+    const size_t need = e.bytes_needed();
+    if (need > (size_t)TTM_NOALLOC_SCRATCH_BYTES)
+      throw Error(TTM_ERR_WORKSPACE, "the product needs " + std::to_string(need) +
+                                         " bytes of workspace; the allocation-free path has " +
+                                         std::to_string((size_t)TTM_NOALLOC_SCRATCH_BYTES));
+    std::vector<ttm_report> reps(1);
+    std::memset(&reps[0], 0, sizeof(ttm_report));
+    e.execute(info.scratch, o, &reps, out);
+  } catch (const Error& err) {
+    return set_err(err.status, err.what());
+  } catch (const std::exception& ex) {
+    return set_err(TTM_ERR_INVALID_ARG, ex.what());
+  }
   return TTM_OK;
 }
 
