@@ -171,8 +171,12 @@ class Engine {
     ++launches_;
   }
   // Cooperative launch of 256-thread CTAs with one warp per work item (`units` items per round).
+  // The kernels hand work item i to warp i / gridDim.x of CTA i % gridDim.x, so one CTA per
+  // item (up to full co-residency) spreads a round over as many SMs as it has items: the
+  // float64 pipe of every SM works, instead of a few SMs running eight items each.
   void coop(void* fn, void* args, int blocks_per_sm, long units, int units_per_cta = 8) {
-    long blocks = std::max(1L, std::min((long)blocks_per_sm * hs_.num_sms, (units + units_per_cta - 1) / units_per_cta));
+    (void)units_per_cta;
+    long blocks = std::max(1L, std::min((long)blocks_per_sm * hs_.num_sms, units));
     void* kargs[] = {args};
     TTM_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), kargs, 0, hs_.stream));
     ++launches_;
