@@ -86,6 +86,9 @@ typedef struct {
   int32_t check_finite;     /* 1: scan inputs for NaN/Inf on the device                  */
   int32_t profile_kernels;  /* 1: time every one-sided Jacobi launch with CUDA events on
                                the handle's stream (fills the jacobi_* report fields)      */
+  int32_t f32_passes;       /* float32 preconditioning passes of every Swap SVD before the
+                               float64 polish: 0 = library default (3), 1..8 accepted     */
+  int32_t reserved0;        /* must be 0                                                 */
 } ttm_options;
 
 /* Filled by ttm_multiply. All fields are host values once the call returns. */
@@ -106,8 +109,11 @@ typedef struct {
   int64_t n_kernel_launches;   /* kernels this call launched (all products of a batch)   */
   int64_t jacobi_launches;     /* one-sided Jacobi launches                               */
   double jacobi_ms;            /* their summed device time (profile_kernels = 1), else 0 */
-  double jacobi_flops;         /* float64 flops the Jacobi kernels executed (counted on
+  double jacobi_flops;         /* float64 flops the polish kernels executed (counted on
                                   the device: dot products and applied rotations)         */
+  double jacobi32_ms;          /* device time of the float32 preconditioning passes
+                                  (profile_kernels = 1), else 0                           */
+  double jacobi32_flops;       /* float32 flops those passes executed                      */
 } ttm_report;
 
 /* Creates a handle bound to CUDA device `device` and stream `cuda_stream`

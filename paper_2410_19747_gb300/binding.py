@@ -41,7 +41,8 @@ class c_tt(ctypes.Structure):
 class c_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("eps", ctypes.c_double), ("chi_max", ctypes.c_int64),
                 ("chi_out", ctypes.c_int64), ("max_sweeps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("check_finite", ctypes.c_int32), ("profile_kernels", ctypes.c_int32)]
+                ("check_finite", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
+                ("f32_passes", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class c_report(ctypes.Structure):
@@ -52,7 +53,8 @@ class c_report(ctypes.Structure):
                 ("peak_workspace_bytes", ctypes.c_int64), ("bond_trace", ctypes.POINTER(ctypes.c_int64)),
                 ("bond_trace_len", ctypes.c_int64), ("n_kernel_launches", ctypes.c_int64),
                 ("jacobi_launches", ctypes.c_int64), ("jacobi_ms", ctypes.c_double),
-                ("jacobi_flops", ctypes.c_double)]
+                ("jacobi_flops", ctypes.c_double), ("jacobi32_ms", ctypes.c_double),
+                ("jacobi32_flops", ctypes.c_double)]
 
 
 _LIB = None
@@ -102,9 +104,10 @@ def _check(status):
         raise TTMError(status, _LIB.ttm_last_error().decode())
 
 
-def make_options(prec="fp64", eps=0.0, chi_max=0, chi_out=0, max_sweeps=0, use_graph=0, profile=0):
+def make_options(prec="fp64", eps=0.0, chi_max=0, chi_out=0, max_sweeps=0, use_graph=0, profile=0,
+                 f32_passes=0):
     return c_options(PREC[prec] if isinstance(prec, str) else int(prec), float(eps), int(chi_max),
-                     int(chi_out), int(max_sweeps), int(use_graph), 0, int(profile))
+                     int(chi_out), int(max_sweeps), int(use_graph), 0, int(profile), int(f32_passes), 0)
 
 
 class TTDesc:
@@ -213,11 +216,12 @@ def _shape_out(o, bufs, d):
     return cores
 
 
-def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0):
+def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
+                         f32_passes=0):
     """[(A_i, B_i)] -> ([Omega_i], [report_i]) with one batched launch sequence (ttm_multiply_batched)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
-                       profile=profile)
+                       profile=profile, f32_passes=f32_passes)
     n = len(pairs)
     da = [TTDesc(A) for A, _ in pairs]
     db = [TTDesc(B) for _, B in pairs]
@@ -244,11 +248,12 @@ def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp6
     return results, [report_dict(reps[i], traces[i]) for i in range(n)]
 
 
-def ttm_multiply(handle, A, B, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0):
+def ttm_multiply(handle, A, B, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
+                 f32_passes=0):
     """Omega = A o B through ttm_multiply. Returns (cores, report)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
-                       profile=profile)
+                       profile=profile, f32_passes=f32_passes)
     a, b = TTDesc(A), TTDesc(B)
     o = make_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out)
     cap = int(lib.ttm_output_capacity(ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(o)))

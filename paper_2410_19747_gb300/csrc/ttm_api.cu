@@ -91,7 +91,9 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
   note_carriage(bl, nbnd);
   note_carriage(nbnd, br);
   const int wslot = ST_NFIXED + n_trunc_++;
-  const int sw32 = jac_launch_++;
+  const int npass = f32_passes();
+  const int sw32 = jac_launch_;
+  jac_launch_ += npass;
   const int sw64 = jac_launch_++;
   if (launch_) {
     const Dim m{d_, bl}, n{d_, br};
@@ -99,43 +101,63 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
     const long pairs = (long)Z_ * (npad_ub / 2);
     // 1. Theta = X Y with the physical legs permuted, column-major m x n (Fig. 1C)
     gemm(ThetaFn{tab_, x, y, ws(WS_T), bl, bm, br, d_}, d_ * d_, umax(bl), umax(br));
-    // 2. float32 one-sided Jacobi on a float copy: the rotation V32 (preconditioner)
-    cast(ws(WS_T), ws(WS_W32), m, n, 1, (long)m_ub * n_ub);
-    HestArgs h32{tab_, ws(WS_W32), ws(WS_V32), m, n, npad_ub, 30,
-                 counters_ + (size_t)sw32 * counter_stride_,
-                 16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)), 64 * 5.96e-8,
-                 fro2_ + (size_t)sw32 * Z_, 1, ST_JFLOPS32, ws(WS_NRM), -1};
-    coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs);
-    // 3. V0 = Q of a float64 Householder QR of V32: orthonormal to float64 rounding
-    cast(ws(WS_V32), ws(WS_X), n, n, 0, (long)n_ub * n_ub);
-    QRArgs qa{tab_, ws(WS_X), ws(WS_TAU), ws(WS_R), ws(WS_V), n, n, nscr, n_ub, n_ub};
-    coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8);
-    // 4. W = Theta V0 in float64: Theta = W V0^T holds exactly up to rounding
-    gemm(ThetaVFn{tab_, ws(WS_T), ws(WS_V), ws(WS_X), m, n}, 1, m_ub, n_ub);
-    // 5. float64 polish of all column pairs from the float32 starting point: the column
-    //    norms become the singular values to float64 accuracy, so the rank rule and the
-    //    discarded weight of Eq. eps are decided in float64.
-    {
-      cudaEvent_t pe0 = nullptr, pe1 = nullptr;
-      if (opt_.profile_kernels) {
-        pe0 = prof_event();
-        pe1 = prof_event();
-        TTM_CUDA(cudaEventRecord(pe0, hs_.stream));
+    // 2. float32 preconditioning passes. Each pass runs a float32 one-sided Jacobi on a
+    //    float copy of the current W (V32 starts at I), makes V32 orthonormal to float64
+    //    rounding by a float64 Householder QR (V32 = Q R), and applies Q to W and V in
+    //    float64, so W V^T = Theta keeps holding exactly up to rounding. The first pass
+    //    works on Theta itself, whose float copy only resolves singular values above about
+    //    u32 ||Theta||; it stops at an absolute floor at that level. After it the columns
+    //    of W are graded (norms near the singular values), so a float copy keeps each
+    //    column to relative accuracy, and the later passes (relative test only, floor at
+    //    float64 rounding) resolve the rest of the spectrum. The float64 polish then starts
+    //    from couplings near the float32 test and converges in a few sweeps.
+    int wb = ws(WS_T), wo = ws(WS_X);            // current W, spare m x n buffer
+    int vb = -1;                                 // current V (-1: identity)
+    int vf[2] = {ws(WS_V2), ws(WS_V3)};          // free n x n buffers
+    int vspare = ws(WS_V);
+    for (int p = 0; p < npass; ++p) {
+      cast(wb, ws(WS_W32), m, n, 1, (long)m_ub * n_ub);
+      HestArgs h32{tab_, ws(WS_W32), ws(WS_V32), m, n, npad_ub, kF32Sweeps,
+                   counters_ + (size_t)(sw32 + p) * counter_stride_,
+                   16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)),
+                   p == 0 ? 64 * 5.96e-8 : 64 * 1.11e-16,
+                   fro2_ + (size_t)(sw32 + p) * Z_, 1, ST_JFLOPS32, ws(WS_NRM), -1};
+      timed(1, [&] { coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs); });
+      // V32 -> float64 (QR input, overwritten by the reflectors) -> Q
+      const int qin = vf[0], qout = (vb < 0) ? vspare : vf[1];
+      cast(ws(WS_V32), qin, n, n, 0, (long)n_ub * n_ub);
+      QRArgs qa{tab_, qin, ws(WS_TAU), ws(WS_R), qout, n, n, nscr, n_ub, n_ub};
+      coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8);
+      // W <- W Q (float64)
+      gemm(ThetaVFn{tab_, wb, qout, wo, m, n}, 1, m_ub, n_ub);
+      std::swap(wb, wo);
+      if (vb < 0) {
+        vb = qout;                               // V = I Q; vf[0], vf[1] stay free
+      } else {
+        // V <- V Q into the consumed QR input; the old V and Q become free
+        gemm(ThetaVFn{tab_, vb, qout, qin, n, n}, 1, n_ub, n_ub);
+        vf[0] = vb;
+        vf[1] = qout;
+        vb = qin;
       }
+    }
+    // 3. float64 polish of all column pairs: the column norms become the singular values
+    //    to float64 accuracy, so the rank rule and the discarded weight of Eq. eps are
+    //    decided in float64.
+    {
       const int polish_sweeps =
           opt_.prec == TTM_PREC_MIXED_F32 ? (opt_.max_sweeps > 0 ? opt_.max_sweeps : 3) : max_sweeps();
-      HestArgs h64{tab_, ws(WS_X), ws(WS_V), m, n, npad_ub, polish_sweeps,
+      HestArgs h64{tab_, wb, vb, m, n, npad_ub, polish_sweeps,
                    counters_ + (size_t)sw64 * counter_stride_,
                    1e-10, 64 * 1.11e-16,
                    fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), -1};
-      coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs);
-      if (opt_.profile_kernels) TTM_CUDA(cudaEventRecord(pe1, hs_.stream));
+      timed(0, [&] { coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs); });
     }
-    // 6. final order by column norm, Eq. eps + cap, new carriages
-    order_and_truncate(m, n, nbnd, 1, wslot, n_ub);
+    // 4. final order by column norm, Eq. eps + cap, new carriages
+    order_and_truncate(wb, m, n, nbnd, 1, wslot, n_ub);
     {
       ++launches_;
-      GatherArgs ga{tab_, ws(WS_X), ws(WS_V), ws(WS_PERM), y, x, bl, br, nbnd, d_};
+      GatherArgs ga{tab_, wb, vb, ws(WS_PERM), y, x, bl, br, nbnd, d_};
       dim3 g3(cdiv(std::max(m_ub, n_ub), 128), k_ub, Z_);
       swap_gather_kernel<<<g3, 128, 0, hs_.stream>>>(ga);
       TTM_CUDA(cudaGetLastError());
@@ -145,9 +167,10 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
 }
 
 // Column norms of W (workspace X), descending order, and the rank rule of Eq. eps.
-void Engine::order_and_truncate(Dim m, Dim n, int ibond, int record, int wslot, int n_ub, int ieps) {
+void Engine::order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, int wslot, int n_ub,
+                                int ieps) {
   launches_ += 3;
-  NormArgs na{tab_, ws(WS_X), ws(WS_NRM), m, n};
+  NormArgs na{tab_, wbuf, ws(WS_NRM), m, n};
   dim3 g(cdiv(n_ub, 8), Z_);
   colnorm_kernel<<<g, 256, 0, hs_.stream>>>(na);
   TTM_CUDA(cudaGetLastError());
@@ -264,9 +287,10 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   char* base = (char*)arena;
   size_t off = 0;
   hbuf_.assign((size_t)Z_ * nb_, nullptr);
-  const long ws_elems[WS_COUNT] = {t_elems_, v_elems_, vec_elems_, vec_elems_, vec_elems_,
-                                   vec_elems_, r_elems_, q_elems_, t_elems_ / 2 + 1, v_elems_ / 2 + 1,
-                                   x_elems_};
+  const long ws_elems[] = {t_elems_,   v_elems_, vec_elems_, vec_elems_, vec_elems_,
+                           vec_elems_, r_elems_, q_elems_,   t_elems_ / 2 + 1, v_elems_ / 2 + 1,
+                           x_elems_,   v_elems_, v_elems_};
+  static_assert(sizeof(ws_elems) / sizeof(ws_elems[0]) == WS_COUNT, "one size per workspace");
   for (int z = 0; z < Z_; ++z) {
     for (int bi = 0; bi < nchain_; ++bi) {
       hbuf_[(size_t)z * nb_ + bi] = (double*)(base + off);
@@ -288,7 +312,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   off = align256(off + (size_t)Z_ * ns * sizeof(double));
   d_istat_ = (int*)(base + off);
   off = align256(off + (size_t)Z_ * nis * sizeof(int));
-  counter_stride_ = Z_ * max_sweeps();
+  counter_stride_ = Z_ * counter_sweeps();
   counters_ = (int*)(base + off);
   const int n_jac = std::max(1, jac_launch_);
   off = align256(off + (size_t)n_jac * counter_stride_ * sizeof(int));
@@ -312,6 +336,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   // second walk: launch
   launches_ = 0;
   prof_used_ = 0;
+  prof_kind_.clear();
   const int nchain_planned = nchain_;
   const int jac_planned = jac_launch_;
   launch_ = true;
@@ -331,11 +356,14 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   TTM_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   if (hs_.ev0 && hs_.ev1) TTM_CUDA(cudaEventElapsedTime(&ms, hs_.ev0, hs_.ev1));
-  double jac_ms = 0.0;
+  double jac_ms = 0.0, jac32_ms = 0.0;
   for (int q = 0; q + 1 < prof_used_; q += 2) {
     float x = 0.f;
     TTM_CUDA(cudaEventElapsedTime(&x, hs_.prof_events[q], hs_.prof_events[q + 1]));
-    jac_ms += x;
+    if (prof_kind_[q / 2] == 1)
+      jac32_ms += x;
+    else
+      jac_ms += x;
   }
 
   for (int z = 0; z < Z_; ++z) {
@@ -395,6 +423,8 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     r.jacobi_launches = jac_launch_;
     r.jacobi_ms = jac_ms;
     r.jacobi_flops = stat[(size_t)0 * ns + ST_JFLOPS];  // float64 polish, launch-wide (all products)
+    r.jacobi32_ms = jac32_ms;
+    r.jacobi32_flops = stat[(size_t)0 * ns + ST_JFLOPS32];
     r.bond_trace = (int64_t*)user_trace;
     r.bond_trace_len = 0;
     if (user_trace) {
@@ -454,6 +484,9 @@ static ttm_status check_opts(const ttm_options& o) {
     return set_err(TTM_ERR_UNSUPPORTED, "tensor-core split precision modes are not built");
   if (o.chi_out > 0 && (o.chi_max == 0 || o.chi_out < o.chi_max))
     return set_err(TTM_ERR_UNSUPPORTED, "chi_out below chi_max (final rounding) is not built yet");
+  if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)
+    return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
+  if (o.reserved0 != 0) return set_err(TTM_ERR_INVALID_ARG, "reserved option field must be 0");
   return TTM_OK;
 }
 

@@ -52,7 +52,10 @@ class Engine {
   long max_carriage() const { return carriage_elems_; }
 
  private:
-  enum { WS_T = 0, WS_V, WS_NRM, WS_SORT, WS_PERM, WS_TAU, WS_R, WS_Q, WS_W32, WS_V32, WS_X, WS_COUNT };
+  enum {
+    WS_T = 0, WS_V, WS_NRM, WS_SORT, WS_PERM, WS_TAU, WS_R, WS_Q, WS_W32, WS_V32, WS_X, WS_V2, WS_V3,
+    WS_COUNT
+  };
 
   HandleState& hs_;
   int Z_;
@@ -127,7 +130,7 @@ class Engine {
   int ws(int w) const { return nchain_ + w; }
 
   size_t per_product_bytes() const {
-    long e = (long)nchain_ * carriage_elems_ + t_elems_ + v_elems_ + 3 * vec_elems_ + vec_elems_ +
+    long e = (long)nchain_ * carriage_elems_ + t_elems_ + 3 * v_elems_ + 3 * vec_elems_ + vec_elems_ +
              r_elems_ + q_elems_ + (t_elems_ / 2 + 1) + (v_elems_ / 2 + 1) + x_elems_;
     // every buffer aligned to 256 bytes
     return (size_t)e * 8 + (size_t)(nb_ + 1) * 256;
@@ -138,11 +141,17 @@ class Engine {
     b += (size_t)Z_ * ub_.size() * sizeof(int) + 256;
     b += (size_t)Z_ * (ST_NFIXED + n_trunc_) * sizeof(double) + 256;
     b += (size_t)Z_ * IS_NFIXED * sizeof(int) + 256;
-    b += (size_t)std::max(1, jac_launch_) * Z_ * max_sweeps() * sizeof(int) + 256;
+    b += (size_t)std::max(1, jac_launch_) * Z_ * counter_sweeps() * sizeof(int) + 256;
     b += (size_t)std::max(1, jac_launch_) * Z_ * sizeof(double) + 256;
     return b;
   }
   int max_sweeps() const { return opt_.max_sweeps > 0 ? opt_.max_sweeps : kDefaultSweeps; }
+  // Sweep counters per product and Jacobi launch: room for the float64 limit and for the
+  // fixed limit of the float32 passes.
+  int counter_sweeps() const { return std::max(max_sweeps(), kF32Sweeps); }
+  int f32_passes() const {
+    return opt_.f32_passes > 0 ? std::min(opt_.f32_passes, kMaxF32Passes) : kDefaultF32Passes;
+  }
 
   // grid helpers
   static unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
@@ -183,6 +192,7 @@ class Engine {
   }
   long launches_ = 0;
   int prof_used_ = 0;
+  std::vector<int> prof_kind_;  // per event pair: 0 float64 polish, 1 float32 pass
   cudaEvent_t prof_event() {
     if (prof_used_ >= (int)hs_.prof_events.size()) {
       cudaEvent_t e;
@@ -191,12 +201,25 @@ class Engine {
     }
     return hs_.prof_events[prof_used_++];
   }
+  // Brackets a Jacobi launch with a pair of events when kernel profiling is on.
+  template <class Launch>
+  void timed(int kind, Launch&& launch) {
+    if (!opt_.profile_kernels) {
+      launch();
+      return;
+    }
+    cudaEvent_t e0 = prof_event(), e1 = prof_event();
+    prof_kind_.push_back(kind);
+    TTM_CUDA(cudaEventRecord(e0, hs_.stream));
+    launch();
+    TTM_CUDA(cudaEventRecord(e1, hs_.stream));
+  }
 
   // ------------------------------------------------------------------ steps
   void load_core(const ttm_tt* T, int k, int buf);
   void qr_move(int c, int& nx, int bl, int& br, int brr);
   int swap(int x, int y, int bl, int bm, int br);
-  void order_and_truncate(Dim m, Dim n, int ibond, int record, int wslot, int n_ub, int ieps = -1);
+  void order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, int wslot, int n_ub, int ieps = -1);
   void contract(int kb, int mb, int out, int il, int ia, int ir);
   void run();
 };

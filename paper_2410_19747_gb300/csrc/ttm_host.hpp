@@ -28,6 +28,9 @@ struct Error : std::runtime_error {
 
 constexpr int kMaxBond = 8192;      // largest bond the planner accepts
 constexpr int kDefaultSweeps = 40;  // one-sided Jacobi sweep limit
+constexpr int kDefaultF32Passes = 3;  // float32 preconditioning passes of every Swap SVD
+constexpr int kMaxF32Passes = 8;
+constexpr int kF32Sweeps = 30;  // sweep limit of every float32 pass
 
 struct DeviceArena {
   void* ptr = nullptr;

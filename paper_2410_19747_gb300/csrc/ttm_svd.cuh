@@ -144,7 +144,6 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
     for (int r = 0; r < a.npad_ub - 1; ++r) {
       for (long it = gwarp; it < items; it += nwarps) {
         const int z = (int)(it / half), i = (int)(it % half);
-        if (sweep > 0 && ldcg_int(&a.counters[z * a.max_sweeps + sweep - 1]) == 0) continue;
         const int n = a.n.eval(a.t, z);
         const int npad = n + (n & 1);
         if (i >= npad / 2 || r >= npad - 1) continue;
@@ -156,21 +155,41 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
           q = (r - i + npad - 1) % (npad - 1);
         }
         if (p >= n || q >= n) continue;
+        const int m = a.m.eval(a.t, z);
         int* mark = reinterpret_cast<int*>(bufp(a.t, z, a.bmark));
-        if (sweep >= 1 && __ldcg(&mark[p]) < sweep - 1 && __ldcg(&mark[q]) < sweep - 1) continue;
+        T* W = reinterpret_cast<T*>(bufp(a.t, z, a.bw));
+        T* wp = W + (long)p * m;
+        T* wq = W + (long)q * m;
+        // Every load of the pair is issued before any of them is tested: the product's
+        // convergence counter, both marks, ||W||_F^2 and the first chunk of both columns
+        // travel together, so a round costs one memory round trip instead of several.
+        const int prev = sweep > 0 ? ldcg_int(&a.counters[z * a.max_sweeps + sweep - 1]) : 1;
+        const int mp = sweep >= 1 ? ldcg_int(&mark[p]) : 0;
+        const int mq = sweep >= 1 ? ldcg_int(&mark[q]) : 0;
+        const double fro2 = __ldcg(&a.fro2[z]);
+        T x[kChunk], y[kChunk];
+        load_chunk(wp, wq, 0, m, lane, x, y);
+        // float32: the two columns of V ride along when they fit one chunk (the rotation
+        // of V needs only c and s), which removes the last dependent round trip.
+        T* V = reinterpret_cast<T*>(bufp(a.t, z, a.bv));
+        T* vp = V + (long)p * n;
+        T* vq = V + (long)q * n;
+        constexpr bool kPrefetchV = sizeof(T) == 4;
+        T vx[kPrefetchV ? kChunk : 1], vy[kPrefetchV ? kChunk : 1];
+        const bool vpre = kPrefetchV && n <= 32 * kChunk;
+        if constexpr (kPrefetchV) {
+          if (vpre) load_chunk(vp, vq, 0, n, lane, vx, vy);
+        }
+        if (prev == 0) continue;
+        if (sweep >= 1 && mp < sweep - 1 && mq < sweep - 1) continue;
         if (a.bcls >= 0) {
           const int* cls = reinterpret_cast<const int*>(bufp(a.t, z, a.bcls));
           const int mode = cls[n];
           if (mode == 0 || (mode == 1 && cls[p] == cls[q])) continue;
         }
-        const int m = a.m.eval(a.t, z);
-        T* W = reinterpret_cast<T*>(bufp(a.t, z, a.bw));
-        T* wp = W + (long)p * m;
-        T* wq = W + (long)q * m;
-        T x[kChunk], y[kChunk];
         T al = 0, be = 0, ga = 0;
         for (int base = 0; base < m; base += 32 * kChunk) {
-          load_chunk(wp, wq, base, m, lane, x, y);
+          if (base > 0) load_chunk(wp, wq, base, m, lane, x, y);
 #pragma unroll
           for (int k = 0; k < kChunk; ++k) {
             if (base + 32 * k < m) {  // warp-uniform: skips the zero padding of a short column
@@ -184,7 +203,7 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
         be = warp_sum_t(be);
         ga = warp_sum_t(ga);
         flops += 6.0 * m;
-        const double fro = sqrt(__ldcg(&a.fro2[z]));
+        const double fro = sqrt(fro2);
         const double aga = fabs((double)ga);
         const double big = sqrt((double)(al > be ? al : be));
         if (ga != T(0) && aga > a.tol * sqrt((double)al) * sqrt((double)be) && aga > a.delta * big * fro) {
@@ -197,8 +216,14 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
             store_rotated(wp, wq, 0, m, lane, x, y, c, s);
           else
             rotate_columns(wp, wq, m, lane, c, s);
-          T* V = reinterpret_cast<T*>(bufp(a.t, z, a.bv));
-          rotate_columns(V + (long)p * n, V + (long)q * n, n, lane, c, s);
+          if constexpr (kPrefetchV) {
+            if (vpre)
+              store_rotated(vp, vq, 0, n, lane, vx, vy, c, s);
+            else
+              rotate_columns(vp, vq, n, lane, c, s);
+          } else {
+            rotate_columns(vp, vq, n, lane, c, s);
+          }
           flops += 6.0 * m + 6.0 * n;
           if (lane == 0) {
             atomicAdd(&a.counters[z * a.max_sweeps + sweep], 1);
