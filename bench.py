@@ -194,6 +194,52 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def jacobi_roofline(reps, t_local):
+    """Roofline object of the dominant one-sided Jacobi kernel of the timed steps (device
+    time from CUDA events on the library's stream, flops counted on the device), with the
+    other Jacobi kernel attached under "other_kernels"."""
+    kernels = []
+    n_sw = sum(r["n_swaps"] for r in reps)
+    for name, ms_key, fl_key, peak, src, n_l in (
+            ("hestenes_kernel<double> (one-sided Jacobi polish, float64)", "jacobi_ms", "jacobi_flops",
+             FP64_PEAK_TFLOPS, "nominal float64 rate: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz", n_sw),
+            ("hestenes_kernel<float> (one-sided Jacobi preconditioning passes, float32)", "jacobi32_ms",
+             "jacobi32_flops", FP32_PEAK_TFLOPS, "nominal float32 rate: 128 FFMA/clk/SM x 152 SMs x 2.07 GHz",
+             sum(r["jacobi_launches"] for r in reps) - n_sw)):
+        ms = sum(r[ms_key] for r in reps)
+        fl = sum(r[fl_key] for r in reps)
+        ach = (fl / (ms / 1e3) / 1e12) if ms > 0 else None
+        kernels.append({"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "peak_source": src, "frac": (ach / peak) if ach else None, "traffic": None,
+                        "share_of_step": ms / 1e3 / t_local if t_local > 0 else None,
+                        "launches": n_l, "avg_launch_ms": ms / max(1, n_l)})
+    kernels.sort(key=lambda k: -(k["share_of_step"] or 0.0))
+    roof = dict(kernels[0])
+    roof["other_kernels"] = kernels[1:]
+    return roof
+
+
+def make_line(args, reps, t_local, t, world, e2e, clocks):
+    """The bench JSON line (without cpu_baseline) from the reports of the timed steps.
+    t_local: this rank's summed step time; t: the max over ranks."""
+    r0 = reps[-1]
+    products = world * args.steps
+    flops = float(np.mean([r["flops_counted"] for r in reps]))
+    return {
+        "metric": METRIC, "value": products / t, "unit": "products/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config(args),
+        "tflops_counted": flops * products / t / 1e12,
+        "roofline": jacobi_roofline(reps, t_local),
+        "e2e": e2e,
+        "gpu_launches": int(sum(r["n_kernel_launches"] for r in reps)),
+        "clocks": clocks,
+        "report": {k: r0[k] for k in ("n_swaps", "n_contracts", "n_qr", "max_bond", "discarded_weight",
+                                      "err_bound", "norm_out", "jacobi_sweeps_max")},
+    }
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -247,8 +293,6 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
         dist.barrier()
-    products = world * args.steps
-    value = products / t
 
     # end to end through the public call from pinned host buffers
     e2e_t, h2d, d2h, e2e_err = 0.0, 0, 0, None
@@ -271,41 +315,11 @@ def main():
         e2e_val = world * args.e2e_steps / float(ev.item())
 
     if rank == 0:
-        r0 = reps[-1]
+        line = make_line(args, reps, t_local, t, world,
+                         {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d,
+                          "d2h_bytes_per_step": d2h, **({"error": e2e_err} if e2e_err else {})},
+                         clk.summary())
         flops = float(np.mean([r["flops_counted"] for r in reps]))
-        # the two Jacobi kernels, timed with events on the library's stream
-        kernels = []
-        n_sw = sum(r["n_swaps"] for r in reps)
-        for name, ms_key, fl_key, peak, src, n_l in (
-                ("hestenes_kernel<double> (one-sided Jacobi polish, float64)", "jacobi_ms", "jacobi_flops",
-                 FP64_PEAK_TFLOPS, "nominal float64 rate: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz", n_sw),
-                ("hestenes_kernel<float> (one-sided Jacobi preconditioning passes, float32)", "jacobi32_ms",
-                 "jacobi32_flops", FP32_PEAK_TFLOPS, "nominal float32 rate: 128 FFMA/clk/SM x 152 SMs x 2.07 GHz",
-                 sum(r["jacobi_launches"] for r in reps) - n_sw)):
-            ms = sum(r[ms_key] for r in reps)
-            fl = sum(r[fl_key] for r in reps)
-            ach = (fl / (ms / 1e3) / 1e12) if ms > 0 else None
-            kernels.append({"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                            "peak_source": src, "frac": (ach / peak) if ach else None, "traffic": None,
-                            "share_of_step": ms / 1e3 / t_local if t_local > 0 else None,
-                            "launches": n_l, "avg_launch_ms": ms / max(1, n_l)})
-        kernels.sort(key=lambda k: -(k["share_of_step"] or 0.0))
-        roof = dict(kernels[0])
-        roof["other_kernels"] = kernels[1:]
-        line = {
-            "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(args),
-            "tflops_counted": flops * products / t / 1e12,
-            "roofline": roof,
-            "e2e": {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    **({"error": e2e_err} if e2e_err else {})},
-            "gpu_launches": int(sum(r["n_kernel_launches"] for r in reps)),
-            "clocks": clk.summary(),
-            "report": {k: r0[k] for k in ("n_swaps", "n_contracts", "n_qr", "max_bond", "discarded_weight",
-                                          "err_bound", "norm_out", "jacobi_sweeps_max")},
-        }
         if not args.no_cpu_baseline:
             v, spent, desc = cpu_baseline(args, flops, swap_model_flops(args.chi))
             line["cpu_baseline"] = {"value": v, "unit": "products/s", "cores": os.cpu_count(), "kind": "oracle",
