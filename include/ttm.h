@@ -82,8 +82,10 @@ typedef struct {
   int64_t chi_max;          /* cap on the bond of every Swap SVD; 0 = unbounded          */
   int64_t chi_out;          /* cap on the output bonds (final TT-SVD rounding); 0 = none */
   int32_t max_sweeps;       /* one-sided Jacobi sweep limit per SVD; 0 = library default */
-  int32_t use_graph;        /* 1: capture the whole sweep in a CUDA graph and replay it  */
-  int32_t check_finite;     /* 1: scan inputs for NaN/Inf on the device                  */
+  int32_t use_graph;        /* reserved for CUDA-graph capture of the sweep: not built,
+                               must be 0 (1 returns TTM_ERR_UNSUPPORTED)                 */
+  int32_t check_finite;     /* reserved for a device scan of the inputs for NaN/Inf: not
+                               built, must be 0 (1 returns TTM_ERR_UNSUPPORTED)          */
   int32_t profile_kernels;  /* 1: time every one-sided Jacobi launch with CUDA events on
                                the handle's stream (fills the jacobi_* report fields)      */
   int32_t f32_passes;       /* float32 preconditioning passes of every Swap SVD before the

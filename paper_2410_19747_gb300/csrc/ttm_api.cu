@@ -484,6 +484,8 @@ static ttm_status check_opts(const ttm_options& o) {
     return set_err(TTM_ERR_UNSUPPORTED, "tensor-core split precision modes are not built");
   if (o.chi_out > 0 && (o.chi_max == 0 || o.chi_out < o.chi_max))
     return set_err(TTM_ERR_UNSUPPORTED, "chi_out below chi_max (final rounding) is not built yet");
+  if (o.use_graph != 0 || o.check_finite != 0)
+    return set_err(TTM_ERR_UNSUPPORTED, "use_graph and check_finite are not built (must be 0)");
   if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)
     return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
   if (o.reserved0 != 0) return set_err(TTM_ERR_INVALID_ARG, "reserved option field must be 0");
