@@ -194,6 +194,22 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def rank_seed(rank):
+    """Seed of the rank's input pair: every rank multiplies its own independent pair (weak
+    scaling; no collective on the data path)."""
+    return 3000 + 10 * rank
+
+
+def max_over_ranks(dist, x, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def jacobi_roofline(reps, t_local):
     """Roofline object of the dominant one-sided Jacobi kernel of the timed steps (device
     time from CUDA events on the library's stream, flops counted on the device), with the
@@ -259,7 +275,7 @@ def main():
     torch.cuda.set_device(dev)
     pkg.build()
     h = pkg.Handle(dev.index)
-    A, B = workload(args.L, args.chi, 3000 + 10 * rank)
+    A, B = workload(args.L, args.chi, rank_seed(rank))
     Ag = [torch.from_numpy(c).to(dev) for c in A]
     Bg = [torch.from_numpy(c).to(dev) for c in B]
     kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec, f32_passes=args.f32_passes)
@@ -287,11 +303,8 @@ def main():
             reps.append(rep)
     torch.cuda.synchronize(dev)
     t_local = sum(dts)
-    t = t_local
+    t = max_over_ranks(dist, t_local, dev)
     if dist:
-        tt = torch.tensor([t_local], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
         dist.barrier()
 
     # end to end through the public call from pinned host buffers
@@ -308,11 +321,8 @@ def main():
             d2h = sum(int(c.numel()) * 8 for c in outh)
     except Exception as ex:  # the device-resident number above stays valid
         e2e_err = repr(ex)
-    e2e_val = world * args.e2e_steps / e2e_t if e2e_t > 0 else None
-    if dist:
-        ev = torch.tensor([e2e_t], device=dev)
-        dist.all_reduce(ev, op=dist.ReduceOp.MAX)
-        e2e_val = world * args.e2e_steps / float(ev.item())
+    e2e_max = max_over_ranks(dist, e2e_t, dev)
+    e2e_val = world * args.e2e_steps / e2e_max if e2e_max > 0 else None
 
     if rank == 0:
         line = make_line(args, reps, t_local, t, world,
