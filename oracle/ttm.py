@@ -7,7 +7,7 @@ in the paper's order and notation:
   psi = M^{w_1} ... M^{w_N}      (the TT "B")
   Omega = Pi^{e_1} ... Pi^{e_N}  (the product A o B)
 
-Readings where the paper is silent or ambiguous (listed in the design doc too):
+Readings where the paper is silent or ambiguous:
   A1  psi enters the concatenated chain reversed, each carriage with its two bond
       legs exchanged: slot N+j holds M_{N+1-j}^T, i.e. Mt[a, s, b] = M[b, s, a].
   A2  after a Swap the singular values go into the carriage that carries the
