@@ -90,7 +90,10 @@ typedef struct {
                                the handle's stream (fills the jacobi_* report fields)      */
   int32_t f32_passes;       /* float32 preconditioning passes of every Swap SVD before the
                                float64 polish: 0 = library default (3), 1..8 accepted     */
-  int32_t reserved0;        /* must be 0                                                 */
+  int32_t f32_block;        /* float32 passes: 0 = scalar one-sided Jacobi (one grid
+                               barrier per round of column pairs, default); 8 or 16 =
+                               block Jacobi on blocks of that many columns (one barrier per
+                               round of block pairs; experimental, not yet run on a GPU)  */
 } ttm_options;
 
 /* Filled by ttm_multiply. All fields are host values once the call returns. */

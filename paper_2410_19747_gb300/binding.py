@@ -42,7 +42,7 @@ class c_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("eps", ctypes.c_double), ("chi_max", ctypes.c_int64),
                 ("chi_out", ctypes.c_int64), ("max_sweeps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("check_finite", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
-                ("f32_passes", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("f32_passes", ctypes.c_int32), ("f32_block", ctypes.c_int32)]
 
 
 class c_report(ctypes.Structure):
@@ -105,9 +105,10 @@ def _check(status):
 
 
 def make_options(prec="fp64", eps=0.0, chi_max=0, chi_out=0, max_sweeps=0, use_graph=0, profile=0,
-                 f32_passes=0):
+                 f32_passes=0, f32_block=0):
     return c_options(PREC[prec] if isinstance(prec, str) else int(prec), float(eps), int(chi_max),
-                     int(chi_out), int(max_sweeps), int(use_graph), 0, int(profile), int(f32_passes), 0)
+                     int(chi_out), int(max_sweeps), int(use_graph), 0, int(profile), int(f32_passes),
+                     int(f32_block))
 
 
 class TTDesc:

@@ -122,7 +122,17 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
                    16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)),
                    p == 0 ? 64 * 5.96e-8 : 64 * 1.11e-16,
                    fro2_ + (size_t)(sw32 + p) * Z_, 1, ST_JFLOPS32, ws(WS_NRM), -1};
-      timed(1, [&] { coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs); });
+      if (opt_.f32_block > 0) {
+        const int fb = opt_.f32_block;
+        const int nblk_ub = (n_ub + fb - 1) / fb;
+        const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
+        BJacArgs bj{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, kF32Sweeps,
+                    h32.counters, h32.tol, h32.delta, h32.fro2, ST_JFLOPS32};
+        void* fn = fb == 8 ? (void*)block_jacobi_kernel<8> : (void*)block_jacobi_kernel<16>;
+        timed(1, [&] { coop(fn, &bj, bjac_blocks_per_sm(fb), (long)Z_ * (nblk_pad_ub / 2)); });
+      } else {
+        timed(1, [&] { coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs); });
+      }
       // V32 -> float64 (QR input, overwritten by the reflectors) -> Q
       const int qin = vf[0], qout = (vb < 0) ? vspare : vf[1];
       cast(ws(WS_V32), qin, n, n, 0, (long)n_ub * n_ub);
@@ -488,7 +498,8 @@ static ttm_status check_opts(const ttm_options& o) {
     return set_err(TTM_ERR_UNSUPPORTED, "use_graph and check_finite are not built (must be 0)");
   if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)
     return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
-  if (o.reserved0 != 0) return set_err(TTM_ERR_INVALID_ARG, "reserved option field must be 0");
+  if (o.f32_block != 0 && o.f32_block != 8 && o.f32_block != 16)
+    return set_err(TTM_ERR_INVALID_ARG, "f32_block must be 0, 8 or 16");
   return TTM_OK;
 }
 

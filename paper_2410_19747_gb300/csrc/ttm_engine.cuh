@@ -18,6 +18,7 @@
 #include "ttm_gemm.cuh"
 #include "ttm_qr.cuh"
 #include "ttm_svd.cuh"
+#include "ttm_bjac.cuh"
 
 namespace ttm {
 
@@ -189,6 +190,19 @@ class Engine {
     void* kargs[] = {args};
     TTM_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), kargs, 0, hs_.stream));
     ++launches_;
+  }
+  // co-resident 256-thread CTAs per SM of the block Jacobi kernels (queried on first use)
+  int bjac_occ_[2] = {0, 0};
+  int bjac_blocks_per_sm(int fb) {
+    int& v = bjac_occ_[fb == 8 ? 0 : 1];
+    if (v == 0) {
+      if (fb == 8)
+        TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, block_jacobi_kernel<8>, 256, 0));
+      else
+        TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, block_jacobi_kernel<16>, 256, 0));
+      if (v < 1) throw Error(TTM_ERR_UNSUPPORTED, "block Jacobi kernel cannot be made resident");
+    }
+    return v;
   }
   long launches_ = 0;
   int prof_used_ = 0;
