@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--f32-passes", type=int, default=0, help="float32 preconditioning passes (0: default)")
+    p.add_argument("--f32-block", type=int, default=0, choices=[0, 8, 16],
+                   help="block width of the float32 Jacobi (0: scalar kernel, the default)")
     return p.parse_args()
 
 
@@ -61,6 +63,8 @@ def config(args):
                         "float64 cores, eps=%g, chi_max=chi_out=%d" % (args.L, args.chi, args.eps, args.chi),
             "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
             "precision_mode": args.prec,
+            "svd": "one-sided Jacobi: %d float32 passes (%s) + float64 polish"
+                   % (args.f32_passes or 3, "block width %d" % args.f32_block if args.f32_block else "scalar"),
             "l2": "flushed between timed steps (256 MiB write outside the timed events)"}
 
 
@@ -278,7 +282,8 @@ def main():
     A, B = workload(args.L, args.chi, rank_seed(rank))
     Ag = [torch.from_numpy(c).to(dev) for c in A]
     Bg = [torch.from_numpy(c).to(dev) for c in B]
-    kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec, f32_passes=args.f32_passes)
+    kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec, f32_passes=args.f32_passes,
+              f32_block=args.f32_block)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
