@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--f32-passes", type=int, default=0, help="float32 preconditioning passes (0: default)")
+    p.add_argument("--batch", type=int, default=1,
+                   help="independent products per step, multiplied in one ttm_multiply_batched call")
     p.add_argument("--f32-block", type=int, default=0, choices=[0, 8, 16],
                    help="block width of the float32 Jacobi (0: scalar kernel, the default)")
     return p.parse_args()
@@ -62,7 +64,7 @@ def config(args):
     return {"workload": "config3: random right-canonical TT pair, L=%d, d=2, chi=%d, sigma_k ~ 1/k, "
                         "float64 cores, eps=%g, chi_max=chi_out=%d" % (args.L, args.chi, args.eps, args.chi),
             "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
-            "precision_mode": args.prec,
+            "precision_mode": args.prec, "batch": getattr(args, "batch", 1),
             "svd": "one-sided Jacobi: %d float32 passes (%s) + float64 polish"
                    % (args.f32_passes or 3, "block width %d" % args.f32_block if args.f32_block else "scalar"),
             "l2": "flushed between timed steps (256 MiB write outside the timed events)"}
@@ -240,10 +242,11 @@ def jacobi_roofline(reps, t_local):
 
 
 def make_line(args, reps, t_local, t, world, e2e, clocks):
-    """The bench JSON line (without cpu_baseline) from the reports of the timed steps.
+    """The bench JSON line (without cpu_baseline) from the reports of the timed steps, one
+    report per step (launch-wide figures: a batched step shares its launches).
     t_local: this rank's summed step time; t: the max over ranks."""
     r0 = reps[-1]
-    products = world * args.steps
+    products = world * args.steps * getattr(args, "batch", 1)
     flops = float(np.mean([r["flops_counted"] for r in reps]))
     return {
         "metric": METRIC, "value": products / t, "unit": "products/s", "n_gpus": world, "steps": args.steps,
@@ -279,16 +282,23 @@ def main():
     torch.cuda.set_device(dev)
     pkg.build()
     h = pkg.Handle(dev.index)
-    A, B = workload(args.L, args.chi, rank_seed(rank))
-    Ag = [torch.from_numpy(c).to(dev) for c in A]
-    Bg = [torch.from_numpy(c).to(dev) for c in B]
+    host_pairs = [workload(args.L, args.chi, rank_seed(rank) + 100 * j) for j in range(args.batch)]
+    pairs = [([torch.from_numpy(c).to(dev) for c in a], [torch.from_numpy(c).to(dev) for c in b])
+             for a, b in host_pairs]
+    Ag, Bg = pairs[0]
     kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec, f32_passes=args.f32_passes,
               f32_block=args.f32_block)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    def step(profile=0):
+        """One step through the public call; returns the step's (launch-wide) report."""
+        if args.batch == 1:
+            return pkg.ttm_multiply(h, Ag, Bg, profile=profile, **kw)[1]
+        return pkg.ttm_multiply_batched(h, pairs, profile=profile, **kw)[1][0]
+
     for _ in range(args.warmup):
-        pkg.ttm_multiply(h, Ag, Bg, **kw)
+        step()
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
@@ -301,7 +311,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            out, rep = pkg.ttm_multiply(h, Ag, Bg, profile=1, **kw)
+            rep = step(profile=1)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             dts.append(e0.elapsed_time(e1) / 1e3)
@@ -315,19 +325,22 @@ def main():
     # end to end through the public call from pinned host buffers
     e2e_t, h2d, d2h, e2e_err = 0.0, 0, 0, None
     try:
-        Ah = [torch.from_numpy(c).pin_memory() for c in A]
-        Bh = [torch.from_numpy(c).pin_memory() for c in B]
+        hp = [([torch.from_numpy(c).pin_memory() for c in a], [torch.from_numpy(c).pin_memory() for c in b])
+              for a, b in host_pairs]
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            outh, rh = pkg.ttm_multiply(h, Ah, Bh, **kw)
+            if args.batch == 1:
+                outs = [pkg.ttm_multiply(h, hp[0][0], hp[0][1], **kw)[0]]
+            else:
+                outs = pkg.ttm_multiply_batched(h, hp, **kw)[0]
             e2e_t += time.perf_counter() - t0
-            h2d = sum(int(c.numel()) * 8 for c in Ah) + sum(int(c.numel()) * 8 for c in Bh)
-            d2h = sum(int(c.numel()) * 8 for c in outh)
+            h2d = sum(int(c.numel()) * 8 for a, b in hp for c in a + b)
+            d2h = sum(int(c.numel()) * 8 for o in outs for c in o)
     except Exception as ex:  # the device-resident number above stays valid
         e2e_err = repr(ex)
     e2e_max = max_over_ranks(dist, e2e_t, dev)
-    e2e_val = world * args.e2e_steps / e2e_max if e2e_max > 0 else None
+    e2e_val = world * args.e2e_steps * args.batch / e2e_max if e2e_max > 0 else None
 
     if rank == 0:
         line = make_line(args, reps, t_local, t, world,

@@ -23,7 +23,7 @@ def fake_report(**over):
 
 def args(**over):
     a = dict(gpus=1, steps=1, warmup=3, impl="ours", chi=512, L=30, eps=1e-14, prec="fp64",
-             no_cpu_baseline=False, e2e_steps=1, f32_passes=0, f32_block=0)
+             no_cpu_baseline=False, e2e_steps=1, f32_passes=0, f32_block=0, batch=1)
     a.update(over)
     return types.SimpleNamespace(**a)
 
@@ -66,6 +66,16 @@ def test_roofline_picks_the_dominant_jacobi_kernel():
 def test_unprofiled_steps_give_no_rate():
     roof = line_for([fake_report(jacobi_ms=0.0, jacobi32_ms=0.0)], 118.0)["roofline"]
     assert roof["achieved"] is None and roof["frac"] is None
+
+
+def test_batched_steps_count_every_product():
+    reps = [fake_report(), fake_report()]             # one launch-wide report per step
+    line = bench.make_line(args(steps=2, batch=4), reps, 200.0, 200.0, 1,
+                           {"value": None, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                           {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0})
+    assert line["value"] == 8 / 200.0
+    assert line["config"]["batch"] == 4
+    assert line["roofline"]["launches"] == 2 * 3 * 435   # launches are shared by the batch
 
 
 def test_several_steps_sum():
