@@ -80,7 +80,10 @@ typedef struct {
   double eps;               /* Eq. eps threshold on the relative discarded weight of every
                                Swap SVD; 0 keeps every singular value                     */
   int64_t chi_max;          /* cap on the bond of every Swap SVD; 0 = unbounded          */
-  int64_t chi_out;          /* cap on the output bonds (final TT-SVD rounding); 0 = none */
+  int64_t chi_out;          /* cap on the output bonds; 0 = none. When chi_out < chi_max
+                               (or chi_max = 0) a final TT-SVD rounding truncates bonds
+                               1..L-1 in order with this cap and the eps rule, leaving the
+                               norm on the last core (built; not yet run on a GPU)        */
   int32_t max_sweeps;       /* one-sided Jacobi sweep limit per SVD; 0 = library default */
   int32_t use_graph;        /* reserved for CUDA-graph capture of the sweep: not built,
                                must be 0 (1 returns TTM_ERR_UNSUPPORTED)                 */

@@ -72,11 +72,15 @@ void Engine::qr_move(int c, int& nx, int bl, int& br, int brr) {
 
 // Swap of X [bl][d][bm] and Y [bm][d][br] (Fig. 1C); Y's buffer receives the new left
 // carriage (the mover, U Lambda), X's buffer the new right one (V^T). Returns the new bond.
-int Engine::swap(int x, int y, int bl, int bm, int br) {
+// kind = SK_ROUND is the same truncated two-site SVD with the physical legs left in place
+// and the output cap chi_out (the final rounding): Y's buffer then receives the new
+// carriage of X's site (U Lambda, leg s) and X's buffer that of Y's site (V^T, leg t).
+int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
+  const long cap = kind == SK_ROUND ? opt_.chi_out : opt_.chi_max;
   std::vector<int> kub(Z_);
   for (int z = 0; z < Z_; ++z) {
     int v = std::min(d_ * ub_[bl][z], d_ * ub_[br][z]);
-    if (opt_.chi_max > 0) v = std::min<long>(v, opt_.chi_max);
+    if (cap > 0) v = std::min<long>(v, cap);
     kub[z] = v;
   }
   const int nbnd = new_bond(kub);
@@ -87,7 +91,7 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
   x_elems_ = std::max(x_elems_, (long)std::max(m_ub, n_ub) * n_ub);
   r_elems_ = std::max(r_elems_, (long)n_ub * n_ub);
   vec_elems_ = std::max(vec_elems_, (long)n_ub + 1);
-  log_.push_back({SK_SWAP, bl, bm, br, nbnd});
+  log_.push_back({kind, bl, bm, br, nbnd});
   note_carriage(bl, nbnd);
   note_carriage(nbnd, br);
   const int wslot = ST_NFIXED + n_trunc_++;
@@ -100,7 +104,8 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
     const int npad_ub = n_ub + (n_ub & 1);
     const long pairs = (long)Z_ * (npad_ub / 2);
     // 1. Theta = X Y with the physical legs permuted, column-major m x n (Fig. 1C)
-    gemm(ThetaFn{tab_, x, y, ws(WS_T), bl, bm, br, d_}, d_ * d_, umax(bl), umax(br));
+    gemm(ThetaFn{tab_, x, y, ws(WS_T), bl, bm, br, d_, kind == SK_ROUND ? 1 : 0}, d_ * d_, umax(bl),
+         umax(br));
     // 2. float32 preconditioning passes. Each pass runs a float32 one-sided Jacobi on a
     //    float copy of the current W (V32 starts at I), makes V32 orthonormal to float64
     //    rounding by a float64 Householder QR (V32 = Q R), and applies Q to W and V in
@@ -164,7 +169,7 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
       timed(0, [&] { coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs); });
     }
     // 4. final order by column norm, Eq. eps + cap, new carriages
-    order_and_truncate(wb, m, n, nbnd, 1, wslot, n_ub);
+    order_and_truncate(wb, m, n, nbnd, 1, wslot, n_ub, cap);
     {
       ++launches_;
       GatherArgs ga{tab_, wb, vb, ws(WS_PERM), y, x, bl, br, nbnd, d_};
@@ -178,7 +183,7 @@ int Engine::swap(int x, int y, int bl, int bm, int br) {
 
 // Column norms of W (workspace X), descending order, and the rank rule of Eq. eps.
 void Engine::order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, int wslot, int n_ub,
-                                int ieps) {
+                                long cap, int ieps) {
   launches_ += 3;
   NormArgs na{tab_, wbuf, ws(WS_NRM), m, n};
   dim3 g(cdiv(n_ub, 8), Z_);
@@ -188,7 +193,7 @@ void Engine::order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, i
   dim3 g2(cdiv(n_ub, 256), Z_);
   rank_kernel<<<g2, 256, 0, hs_.stream>>>(ra);
   TTM_CUDA(cudaGetLastError());
-  TruncArgs ta{tab_, ws(WS_SORT), m, n, ibond, opt_.eps, (int)opt_.chi_max, wslot, record, ieps};
+  TruncArgs ta{tab_, ws(WS_SORT), m, n, ibond, opt_.eps, (int)cap, wslot, record, ieps};
   truncate_kernel<<<Z_, 1024, 0, hs_.stream>>>(ta);
   TTM_CUDA(cudaGetLastError());
 }
@@ -282,6 +287,41 @@ void Engine::run() {
     piL[i] = bA[i - 1];
     piR[i] = mvR;
     record_trace(i);
+  }
+  // a7: final rounding to chi_out, bond 1 first, as a left-to-right TT-SVD sweep. The
+  // sweep leaves Omega right-canonical with the centre on Pi_1. Its mirror (sites reversed,
+  // bond legs exchanged, as in Eq. tensor) is left-canonical with the centre on its last
+  // site, so truncated two-site SVDs from the mirror's right end (U Lambda to the left,
+  // V^T to the right) truncate Omega's bonds 1, 2, ... with the rest of the train
+  // orthonormal; then the mirror is undone. The centre ends on Pi_N.
+  if (rounding()) {
+    std::vector<int> mb(L + 1), mL(L + 1), mR(L + 1);
+    for (int j = 1; j <= L; ++j) {
+      const int src = pi[j], dst = get_buf();
+      const int il = piL[j], ir = piR[j];
+      note_carriage(ir, il);
+      copy2d(LegSwapFn{tab_, src, dst, il, ir, d_}, d_, umax(il), umax(ir));
+      put_buf(src);
+      mb[L + 1 - j] = dst;
+      mL[L + 1 - j] = ir;
+      mR[L + 1 - j] = il;
+    }
+    for (int j = L - 1; j >= 1; --j) {
+      const int nb = swap(mb[j], mb[j + 1], mL[j], mR[j], mR[j + 1], SK_ROUND);
+      std::swap(mb[j], mb[j + 1]);  // the new carriage of mirrored site j sits in the buffer of j + 1
+      mR[j] = nb;
+      mL[j + 1] = nb;
+    }
+    for (int j = 1; j <= L; ++j) {
+      const int src = mb[L + 1 - j], dst = get_buf();
+      const int il = mL[L + 1 - j], ir = mR[L + 1 - j];
+      note_carriage(ir, il);
+      copy2d(LegSwapFn{tab_, src, dst, il, ir, d_}, d_, umax(il), umax(ir));
+      put_buf(src);
+      pi[j] = dst;
+      piL[j] = ir;
+      piR[j] = il;
+    }
   }
   out_buf_.assign(pi.begin() + 1, pi.end());
   out_bond_.assign(L + 1, 0);
@@ -405,8 +445,8 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     r.max_bond = maxb;
     double fl = 0.0;
     for (const StepLog& s : log_) {
-      if (s.kind == SK_SWAP) {
-        r.n_swaps++;
+      if (s.kind == SK_SWAP || s.kind == SK_ROUND) {
+        if (s.kind == SK_SWAP) r.n_swaps++;
         const double Dl = bv(s.b0), Dm = bv(s.b1), Dr = bv(s.b2), k = bv(s.b3);
         const double m = d_ * Dl, n = d_ * Dr;
         fl += 2.0 * d_ * d_ * Dl * Dm * Dr;            // Theta
@@ -447,12 +487,15 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
       r.bond_trace_len = nt;
     }
   }
-  // norm of the output: centre on Pi_1, the other carriages right-orthonormal
+  // norm of the output: the norm of the centre carriage (Pi_1 after the sweep, Pi_N after
+  // the final rounding); every other carriage is orthonormal on the side facing away from it
+  const int centre = rounding() ? L_ - 1 : 0;
   for (int z = 0; z < Z_; ++z) {
     const ttm_tt& o = outs[z];
-    const size_t n = (size_t)o.bonds[0] * d_ * o.bonds[1];
+    const size_t n = (size_t)o.bonds[centre] * d_ * o.bonds[centre + 1];
     std::vector<double> c0(n);
-    TTM_CUDA(cudaMemcpy(c0.data(), hbuf_[(size_t)z * nb_ + out_buf_[0]], n * sizeof(double), cudaMemcpyDeviceToHost));
+    TTM_CUDA(cudaMemcpy(c0.data(), hbuf_[(size_t)z * nb_ + out_buf_[centre]], n * sizeof(double),
+                        cudaMemcpyDeviceToHost));
     double s = 0.0;
     for (double v : c0) s += v * v;
     (*reps)[z].norm_out = std::sqrt(s);
@@ -492,8 +535,6 @@ static ttm_status check_opts(const ttm_options& o) {
     return set_err(TTM_ERR_INVALID_ARG, "unknown precision mode");
   if (o.prec == TTM_PREC_TF32X3 || o.prec == TTM_PREC_BF16X3)
     return set_err(TTM_ERR_UNSUPPORTED, "tensor-core split precision modes are not built");
-  if (o.chi_out > 0 && (o.chi_max == 0 || o.chi_out < o.chi_max))
-    return set_err(TTM_ERR_UNSUPPORTED, "chi_out below chi_max (final rounding) is not built yet");
   if (o.use_graph != 0 || o.check_finite != 0)
     return set_err(TTM_ERR_UNSUPPORTED, "use_graph and check_finite are not built (must be 0)");
   if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)

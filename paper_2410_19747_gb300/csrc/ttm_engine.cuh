@@ -22,7 +22,7 @@
 
 namespace ttm {
 
-enum StepKind { SK_QR = 0, SK_SWAP = 1, SK_CONTRACT = 2 };
+enum StepKind { SK_QR = 0, SK_SWAP = 1, SK_CONTRACT = 2, SK_ROUND = 3 };  // SK_ROUND: final-rounding SVD
 struct StepLog {
   int kind;
   int b0, b1, b2, b3;  // bond ids (meaning per kind)
@@ -232,8 +232,11 @@ class Engine {
   // ------------------------------------------------------------------ steps
   void load_core(const ttm_tt* T, int k, int buf);
   void qr_move(int c, int& nx, int bl, int& br, int brr);
-  int swap(int x, int y, int bl, int bm, int br);
-  void order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, int wslot, int n_ub, int ieps = -1);
+  int swap(int x, int y, int bl, int bm, int br, int kind = SK_SWAP);
+  void order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, int wslot, int n_ub, long cap,
+                          int ieps = -1);
+  // Final rounding (a7): runs when chi_out caps the output below the Swap cap.
+  bool rounding() const { return opt_.chi_out > 0 && (opt_.chi_max == 0 || opt_.chi_out < opt_.chi_max); }
   void contract(int kb, int mb, int out, int il, int ia, int ir);
   void run();
 };

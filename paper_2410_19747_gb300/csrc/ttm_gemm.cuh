@@ -105,11 +105,14 @@ __global__ void __launch_bounds__(256) dgemm_kernel(F f, int nbatch) {
 //   Theta[(l,t),(s,r)] = sum_m X[l,s,m] Y[m,t,r],
 // stored column-major with m_rows = Dl*d rows (row = l*d + t, col = s*Dr + r),
 // which is the layout the one-sided Jacobi SVD works on. Batch b = s*d + t.
+// keep_legs = 1 forms the plain two-site tensor Theta[(l,s),(t,r)] instead (the SVD
+// sweep of the final rounding, where the legs stay in place).
 struct ThetaFn {
   Tables t;
   int bx, by, bth;  // buffers: X, Y, Theta workspace
   int il, im, ir;   // bond ids: left of X, shared, right of Y
   int d;
+  int keep_legs;    // 0: permuted legs (Swap); 1: legs in place
   __device__ GemmDesc operator()(int z, int b) const {
     const int s = b / d, tt = b % d;
     const int Dl = bondv(t, z, il), Dm = bondv(t, z, im), Dr = bondv(t, z, ir);
@@ -117,11 +120,12 @@ struct ThetaFn {
     const double* Y = bufp(t, z, by);
     double* T = bufp(t, z, bth);
     const long mrows = (long)Dl * d;
+    const int row_leg = keep_legs ? s : tt, col_leg = keep_legs ? tt : s;
     GemmDesc g;
     g.M = Dl; g.N = Dr; g.K = Dm;
     g.A = MatRef{X + (long)s * Dm, (long)d * Dm, 1};
     g.B = MatRef{Y + (long)tt * Dr, (long)d * Dr, 1};
-    g.C = OutRef{T + tt + (long)s * Dr * mrows, d, mrows};
+    g.C = OutRef{T + row_leg + (long)col_leg * Dr * mrows, d, mrows};
     g.alpha = 1.0; g.beta = 0.0;
     return g;
   }
