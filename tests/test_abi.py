@@ -58,3 +58,37 @@ def test_invalid_arguments_are_rejected_without_gpu(lib):
     assert b.output_capacity(A, B) == 2 * 2 * 2 or b.output_capacity(A, B) > 0
     bad = [np.zeros((2, 2, 3)), np.zeros((3, 2, 1))]   # boundary bond 2 != 1
     assert b.output_capacity(bad, B) == -1
+
+
+def test_option_validation_without_gpu(lib):
+    """ttm_create validates the options before its first CUDA call."""
+    import ctypes
+    import paper_2410_19747_gb300.binding as b
+    h = ctypes.c_void_p()
+    for kw, status in ((dict(f32_block=5), -1), (dict(f32_passes=9), -1), (dict(f32_passes=-1), -1),
+                       (dict(use_graph=1), -9)):
+        o = b.make_options(**kw)
+        assert lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == status, kw
+    # accepted options get past validation: without a GPU the next step is a CUDA error
+    for kw in (dict(f32_block=8), dict(f32_block=16), dict(f32_passes=1), dict(chi_max=16, chi_out=8),
+               dict(chi_max=0, chi_out=8)):
+        o = b.make_options(**kw)
+        st = lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o))
+        assert st not in (-1, -9), (kw, st, lib.ttm_last_error())
+        if st == 0:
+            lib.ttm_destroy(h)
+
+
+def test_planner_schedules_the_final_rounding_without_gpu(lib):
+    """The host planner walks the whole schedule, final rounding included, with no GPU."""
+    import numpy as np
+    import paper_2410_19747_gb300.binding as b
+    import ttgen
+    A = ttgen.rand_tt(10, 2, 16, 1, canon="left")
+    B = ttgen.rand_tt(10, 2, 16, 2, canon="left")
+    plain = b.output_capacity(A, B, chi_max=32, chi_out=32)
+    assert plain > 0
+    for kw in (dict(chi_max=32, chi_out=12), dict(chi_max=32, chi_out=1), dict(chi_max=0, chi_out=12)):
+        cap = b.output_capacity(A, B, **kw)
+        assert cap >= min(plain, 32 * 2 * 32), kw
+    assert np.isfinite(plain)
