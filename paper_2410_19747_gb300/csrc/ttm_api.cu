@@ -122,7 +122,8 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
     int vspare = ws(WS_V);
     for (int p = 0; p < npass; ++p) {
       cast(wb, ws(WS_W32), m, n, 1, (long)m_ub * n_ub);
-      HestArgs h32{tab_, ws(WS_W32), ws(WS_V32), m, n, npad_ub, kF32Sweeps,
+      const int sweeps32 = (p == 0 && npass > 1) ? kF32FirstPassSweeps : kF32Sweeps;
+      HestArgs h32{tab_, ws(WS_W32), ws(WS_V32), m, n, npad_ub, sweeps32,
                    counters_ + (size_t)(sw32 + p) * counter_stride_,
                    16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)),
                    p == 0 ? 64 * 5.96e-8 : 64 * 1.11e-16,
@@ -131,7 +132,7 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
         const int fb = opt_.f32_block;
         const int nblk_ub = (n_ub + fb - 1) / fb;
         const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
-        BJacArgs bj{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, kF32Sweeps,
+        BJacArgs bj{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, sweeps32,
                     h32.counters, h32.tol, h32.delta, h32.fro2, ST_JFLOPS32};
         void* fn = fb == 8 ? (void*)block_jacobi_kernel<8> : (void*)block_jacobi_kernel<16>;
         timed(1, [&] { coop(fn, &bj, bjac_blocks_per_sm(fb), (long)Z_ * (nblk_pad_ub / 2)); });

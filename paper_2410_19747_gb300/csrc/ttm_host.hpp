@@ -30,7 +30,10 @@ constexpr int kMaxBond = 8192;      // largest bond the planner accepts
 constexpr int kDefaultSweeps = 40;  // one-sided Jacobi sweep limit
 constexpr int kDefaultF32Passes = 3;  // float32 preconditioning passes of every Swap SVD
 constexpr int kMaxF32Passes = 8;
-constexpr int kF32Sweeps = 30;  // sweep limit of every float32 pass
+constexpr int kF32Sweeps = 30;  // sweep limit of the later float32 passes
+// Sweep limit of the first float32 pass: it only has to grade W (the next pass redoes the
+// whole Jacobi on the graded W), so its refining sweeps are dropped.
+constexpr int kF32FirstPassSweeps = 3;
 
 struct DeviceArena {
   void* ptr = nullptr;
