@@ -380,41 +380,6 @@ __global__ void __launch_bounds__(1024) truncate_kernel(TruncArgs a) {
   }
 }
 
-// cls[perm[r]] = (r < k): membership of every column in the kept set.
-// and the polish mode: 1 (kept/dropped pairs only) when the cap clearly binds (the
-// Eq. eps rank exceeds it by a margin, so the kept set is the cap's), else 2 (all pairs).
-struct ClassArgs {
-  Tables t;
-  int bperm, bcls;
-  Dim m, n;
-  int ik, ieps;
-  int cap;
-  double eps;
-};
-__global__ void classify_kernel(ClassArgs a) {
-  const int z = blockIdx.y;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = a.n.eval(a.t, z);
-  const int k = bondv(a.t, z, a.ik);
-  int* cls = reinterpret_cast<int*>(bufp(a.t, z, a.bcls));
-  __syncthreads();
-  if (r == 0) {
-    const int keps = bondv(a.t, z, a.ieps);
-    const int kmax = min(a.m.eval(a.t, z), n);
-    (void)kmax;
-    int mode = 2;
-    if (k >= n) mode = 0;  // every column is kept: W V0^T = Theta is already exact
-    // The kept/dropped split is trusted only when the cap clearly decides it: the Eq. eps
-    // rank exceeds the cap by a margin, and eps is far above the float64 noise of the
-    // column norms (a tiny eps would let rounding-level columns pass as kept).
-    else if (a.cap > 0 && k == a.cap && a.eps >= 1e-18 && keps >= a.cap + max(8, a.cap / 4)) mode = 1;
-    cls[n] = mode;
-  }
-  if (r >= n) return;
-  const int j = reinterpret_cast<const int*>(bufp(a.t, z, a.bperm))[r];
-  cls[j] = (r < k) ? 1 : 0;
-}
-
 // New carriages after a Swap: left[(l, t), j] = W[(l, t), perm[j]] (row-major
 // [Dl][d][k]) and right[j, (s, r)] = V[(s, r), perm[j]] (row-major [k][d][Dr]).
 struct GatherArgs {
