@@ -92,3 +92,24 @@ def test_planner_schedules_the_final_rounding_without_gpu(lib):
         cap = b.output_capacity(A, B, **kw)
         assert cap >= min(plain, 32 * 2 * 32), kw
     assert np.isfinite(plain)
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """A C99 program that includes only include/ttm.h compiles warning-free, links against
+    libttm.so and passes the calls that need no GPU."""
+    import shutil
+    import subprocess
+    import paper_2410_19747_gb300 as pkg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libpath = pkg.library_path()
+    exe = str(tmp_path / "abi_check")
+    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+           "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "abi_check.c"),
+           "-o", exe, libpath, "-Wl,-rpath," + os.path.dirname(libpath)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "c abi check ok" in r.stdout
