@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--f32-passes", type=int, default=0, help="float32 preconditioning passes (0: default)")
     p.add_argument("--batch", type=int, default=1,
                    help="independent products per step, multiplied in one ttm_multiply_batched call")
+    p.add_argument("--polish-kd", type=int, default=0, choices=[0, 1],
+                   help="1: float64 polish of the kept/dropped couplings only where the cap binds")
     p.add_argument("--f32-block", type=int, default=0, choices=[0, 8, 16],
                    help="block width of the float32 Jacobi (0: scalar kernel, the default)")
     return p.parse_args()
@@ -65,8 +67,9 @@ def config(args):
                         "float64 cores, eps=%g, chi_max=chi_out=%d" % (args.L, args.chi, args.eps, args.chi),
             "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
             "precision_mode": args.prec, "batch": getattr(args, "batch", 1),
-            "svd": "one-sided Jacobi: %d float32 passes (%s) + float64 polish"
-                   % (args.f32_passes or 3, "block width %d" % args.f32_block if args.f32_block else "scalar"),
+            "svd": "one-sided Jacobi: %d float32 passes (%s) + float64 polish (%s)"
+                   % (args.f32_passes or 3, "block width %d" % args.f32_block if args.f32_block else "scalar",
+                      "kept/dropped pairs where the cap binds" if getattr(args, "polish_kd", 0) else "all pairs"),
             "l2": "flushed between timed steps (256 MiB write outside the timed events)"}
 
 
@@ -287,7 +290,7 @@ def main():
              for a, b in host_pairs]
     Ag, Bg = pairs[0]
     kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec, f32_passes=args.f32_passes,
-              f32_block=args.f32_block)
+              f32_block=args.f32_block, polish_kept_dropped=args.polish_kd)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 

@@ -97,6 +97,12 @@ typedef struct {
                                barrier per round of column pairs, default); 8 or 16 =
                                block Jacobi on blocks of that many columns (one barrier per
                                round of block pairs; experimental, not yet run on a GPU)  */
+  int32_t polish_kept_dropped; /* 1: when the cap clearly binds a Swap (Eq. eps rank above
+                               the cap by a margin), polish in float64 only the couplings
+                               between kept and dropped columns, which alone decide the
+                               truncated tensor and the discarded weight; 0 (default):
+                               polish all pairs (experimental, not yet run on a GPU)     */
+  int32_t reserved1;        /* must be 0                                                 */
 } ttm_options;
 
 /* Filled by ttm_multiply. All fields are host values once the call returns. */

@@ -42,7 +42,8 @@ class c_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("eps", ctypes.c_double), ("chi_max", ctypes.c_int64),
                 ("chi_out", ctypes.c_int64), ("max_sweeps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("check_finite", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
-                ("f32_passes", ctypes.c_int32), ("f32_block", ctypes.c_int32)]
+                ("f32_passes", ctypes.c_int32), ("f32_block", ctypes.c_int32),
+                ("polish_kept_dropped", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class c_report(ctypes.Structure):
@@ -105,10 +106,10 @@ def _check(status):
 
 
 def make_options(prec="fp64", eps=0.0, chi_max=0, chi_out=0, max_sweeps=0, use_graph=0, profile=0,
-                 f32_passes=0, f32_block=0):
+                 f32_passes=0, f32_block=0, polish_kept_dropped=0):
     return c_options(PREC[prec] if isinstance(prec, str) else int(prec), float(eps), int(chi_max),
                      int(chi_out), int(max_sweeps), int(use_graph), 0, int(profile), int(f32_passes),
-                     int(f32_block))
+                     int(f32_block), int(polish_kept_dropped), 0)
 
 
 class TTDesc:
@@ -218,11 +219,12 @@ def _shape_out(o, bufs, d):
 
 
 def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                         f32_passes=0, f32_block=0):
+                         f32_passes=0, f32_block=0, polish_kept_dropped=0):
     """[(A_i, B_i)] -> ([Omega_i], [report_i]) with one batched launch sequence (ttm_multiply_batched)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
-                       profile=profile, f32_passes=f32_passes, f32_block=f32_block)
+                       profile=profile, f32_passes=f32_passes, f32_block=f32_block,
+                       polish_kept_dropped=polish_kept_dropped)
     n = len(pairs)
     da = [TTDesc(A) for A, _ in pairs]
     db = [TTDesc(B) for _, B in pairs]
@@ -250,11 +252,12 @@ def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp6
 
 
 def ttm_multiply(handle, A, B, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                 f32_passes=0, f32_block=0):
+                 f32_passes=0, f32_block=0, polish_kept_dropped=0):
     """Omega = A o B through ttm_multiply. Returns (cores, report)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
-                       profile=profile, f32_passes=f32_passes, f32_block=f32_block)
+                       profile=profile, f32_passes=f32_passes, f32_block=f32_block,
+                       polish_kept_dropped=polish_kept_dropped)
     a, b = TTDesc(A), TTDesc(B)
     o = make_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out)
     cap = int(lib.ttm_output_capacity(ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(o)))

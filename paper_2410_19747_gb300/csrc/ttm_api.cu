@@ -95,6 +95,10 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
   note_carriage(bl, nbnd);
   note_carriage(nbnd, br);
   const int wslot = ST_NFIXED + n_trunc_++;
+  // kept/dropped polish: bond ids of the provisional rank (after the cap) and the Eq. eps rank
+  const bool kd = opt_.polish_kept_dropped != 0 && kind == SK_SWAP && cap > 0;
+  const int nprov = kd ? new_bond(kub) : -1;
+  const int nepsr = kd ? new_bond(std::vector<int>(Z_, n_ub)) : -1;
   const int npass = f32_passes();
   const int sw32 = jac_launch_;
   jac_launch_ += npass;
@@ -163,10 +167,21 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
     {
       const int polish_sweeps =
           opt_.prec == TTM_PREC_MIXED_F32 ? (opt_.max_sweeps > 0 ? opt_.max_sweeps : 3) : max_sweeps();
+      int bcls = -1;
+      if (kd) {
+        // provisional order and rank from the preconditioned columns, then the membership
+        // of every column (cls in the tau workspace, free during the polish)
+        order_and_truncate(wb, m, n, nprov, 0, -1, n_ub, cap, nepsr);
+        ClassArgs ca{tab_, ws(WS_PERM), ws(WS_TAU), n, nprov, nepsr, (int)cap, opt_.eps};
+        classify_kernel<<<dim3(cdiv(n_ub, 256), Z_), 256, 0, hs_.stream>>>(ca);
+        TTM_CUDA(cudaGetLastError());
+        ++launches_;
+        bcls = ws(WS_TAU);
+      }
       HestArgs h64{tab_, wb, vb, m, n, npad_ub, polish_sweeps,
                    counters_ + (size_t)sw64 * counter_stride_,
                    1e-10, 64 * 1.11e-16,
-                   fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), -1};
+                   fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), bcls};
       timed(0, [&] { coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs); });
     }
     // 4. final order by column norm, Eq. eps + cap, new carriages
@@ -542,6 +557,9 @@ static ttm_status check_opts(const ttm_options& o) {
     return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
   if (o.f32_block != 0 && o.f32_block != 8 && o.f32_block != 16)
     return set_err(TTM_ERR_INVALID_ARG, "f32_block must be 0, 8 or 16");
+  if (o.polish_kept_dropped != 0 && o.polish_kept_dropped != 1)
+    return set_err(TTM_ERR_INVALID_ARG, "polish_kept_dropped must be 0 or 1");
+  if (o.reserved1 != 0) return set_err(TTM_ERR_INVALID_ARG, "reserved option field must be 0");
   return TTM_OK;
 }
 

@@ -380,6 +380,41 @@ __global__ void __launch_bounds__(1024) truncate_kernel(TruncArgs a) {
   }
 }
 
+// Membership of every column in the kept set of a provisional truncation (cls[perm[r]] =
+// (r < k)) and the polish mode of the product in cls[n]: 0 when every column is kept (W V^T
+// = Theta already holds exactly), 1 (kept/dropped pairs only) when the cap clearly decides
+// the kept set, 2 (all pairs) otherwise. The cap decides when the Eq. eps rank exceeds it by
+// a margin and eps is far above the float64 noise of the column norms (a tiny eps would let
+// rounding-level columns pass as kept). Rotations inside the kept or the dropped set leave
+// the truncated tensor W_K V_K^T and the discarded weight ||W_D||_F^2 unchanged.
+struct ClassArgs {
+  Tables t;
+  int bperm, bcls;
+  Dim n;
+  int ik, ieps;  // bond ids: provisional rank (after the cap) and Eq. eps rank
+  int cap;
+  double eps;
+};
+__global__ void classify_kernel(ClassArgs a) {
+  const int z = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = a.n.eval(a.t, z);
+  const int k = bondv(a.t, z, a.ik);
+  int* cls = reinterpret_cast<int*>(bufp(a.t, z, a.bcls));
+  if (r == 0) {
+    const int keps = bondv(a.t, z, a.ieps);
+    int mode = 2;
+    if (k >= n)
+      mode = 0;
+    else if (a.cap > 0 && k == a.cap && a.eps >= 1e-18 && keps >= a.cap + max(8, a.cap / 4))
+      mode = 1;
+    cls[n] = mode;
+  }
+  if (r >= n) return;
+  const int j = reinterpret_cast<const int*>(bufp(a.t, z, a.bperm))[r];
+  cls[j] = (r < k) ? 1 : 0;
+}
+
 // New carriages after a Swap: left[(l, t), j] = W[(l, t), perm[j]] (row-major
 // [Dl][d][k]) and right[j, (s, r)] = V[(s, r), perm[j]] (row-major [k][d][Dr]).
 struct GatherArgs {
