@@ -123,3 +123,26 @@ def test_kept_dropped_polish_is_exact_when_nothing_is_cut(h):
     B = ttgen.rand_tt(10, 2, 8, 1100, canon="left")
     O, rep = run(h, A, B, polish_kept_dropped=1, chi_max=64)
     assert relerr(O, ott.dense(A) * ott.dense(B)) <= 1e-12
+
+
+# ---------------------------------------------------------------- full size (config 3)
+
+def test_full_size_config3_against_the_oracle(h):
+    """chi = 512, L = 30, the benchmark's launch configuration, against the oracle's product
+    on the same inputs (about 90 s on 16 host cores). Properties that hold at any size: the
+    same bond trace, the same total discarded weight, and ||Omega_gpu - Omega_oracle|| small
+    next to ||Omega||, measured with the two-layer environment on the GPU."""
+    import paper_2410_19747_gb300 as pkg
+    A = ttgen.rand_tt_spectral(30, 2, 512, 3000)
+    B = ttgen.rand_tt_spectral(30, 2, 512, 3001)
+    O, rep = run(h, A, B, eps=1e-14, chi_max=512, chi_out=512)
+    Oo, ro = ottm.ttm(A, B, eps=1e-14, chi_max=512, chi_out=512)
+    assert rep["n_swaps"] == 435 and rep["n_contracts"] == 30
+    assert rep["bond_trace"] == ro["bond_trace"]
+    assert abs(rep["discarded_weight"] - ro["discarded_weight"]) <= 1e-6 * ro["discarded_weight"]
+    dev = lambda T: [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in T]
+    g, o = dev(O), dev(Oo)
+    gg, oo, go = pkg.ttm_inner(h, g, g), pkg.ttm_inner(h, o, o), pkg.ttm_inner(h, g, o)
+    # the inner-product form of the distance has a floor near sqrt(u) * ||Omega||
+    assert np.sqrt(max(gg + oo - 2 * go, 0.0) / oo) <= 1e-6
+    assert abs(rep["norm_out"] - np.sqrt(oo)) <= 1e-9 * np.sqrt(oo)
