@@ -1,6 +1,7 @@
-"""GPU checks of paths that have not yet run on a GPU: the final rounding to chi_out < chi_max,
-the block float32 Jacobi (f32_block) and the kept/dropped-only float64 polish
-(polish_kept_dropped). pytest does not collect this module (no test_ prefix). Run it once on
+"""GPU checks that have not yet run on a GPU. They cover three paths: the final rounding to
+chi_out < chi_max, the block float32 Jacobi (f32_block), and the kept/dropped-only float64
+polish (polish_kept_dropped). There is also a full-size (chi = 512, L = 30) product check
+against the oracle. pytest does not collect this module (no test_ prefix). Run it once on
 its own (`python -m pytest tests/gpu_checks_pending.py -x -q`) and rename it to test_*.py
 once it has passed.
 
