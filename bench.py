@@ -1,8 +1,9 @@
 """Benchmark of the GB300 TTM product (one JSON line on rank 0).
 
 Workload (the metric's configuration): two random right-canonical tensor trains,
-L = 30 sites, d = 2, bond chi = 512 with bond spectra shaped like 1/k, float64
-cores; TTM with eps = 1e-14 and chi_max = chi_out = 512. One step = one full
+L = 30 sites, d = 2, bond chi = 512 with a 1/k profile inserted on every bond (the
+realised Schmidt spectra decay faster), float64 cores; TTM with eps = 1e-14 and
+chi_max = chi_out = 512. One step = one full
 product (all N contractions, N(N-1)/2 swaps, all QR gauge moves) through the
 C ABI. Inputs are resident in HBM for `value`; `e2e` repeats the step from
 pinned host buffers with the copies inside the timed region.
@@ -63,8 +64,9 @@ def workload(L, chi, seed):
 
 
 def config(args):
-    return {"workload": "config3: random right-canonical TT pair, L=%d, d=2, chi=%d, sigma_k ~ 1/k, "
-                        "float64 cores, eps=%g, chi_max=chi_out=%d" % (args.L, args.chi, args.eps, args.chi),
+    return {"workload": "config3: random right-canonical TT pair, L=%d, d=2, chi=%d, a 1/k profile on every "
+                        "bond (realised Schmidt spectra steeper), float64 cores, eps=%g, chi_max=chi_out=%d"
+                        % (args.L, args.chi, args.eps, args.chi),
             "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
             "precision_mode": args.prec, "batch": getattr(args, "batch", 1),
             "svd": "one-sided Jacobi: %d float32 passes (%s) + float64 polish (%s)"

@@ -61,12 +61,15 @@ def rand_tt(L, d, chi, seed, canon=None, scale=1.0):
 
 
 def rand_tt_spectral(L, d, chi, seed, decay=1.0):
-    """Right-canonical random TT whose bond spectra are shaped like sigma_j ~ j^-decay.
+    """Right-canonical random TT with a j^-decay profile inserted on every bond.
 
     Each core starts right-orthonormal (QR of a Gaussian (d*D_r) x D_l block,
     transposed); its rows are scaled by a normalised j^-decay profile on its left
-    bond; a final right-to-left QR sweep restores right-canonical form. The
-    realised Schmidt spectra follow the profile approximately, not exactly.
+    bond; a final right-to-left QR sweep restores right-canonical form, norm 1.
+    The profiles of successive bonds compound, so the realised Schmidt spectra
+    decay much faster than the profile. With decay = 1 the middle bond gives
+    log-log slopes of about -3 (L = 12, chi = 16), -4.7 (L = 16, chi = 64) and
+    -6.8 (L = 30, chi = 512); at chi = 512 it spans 1 .. 7e-14.
     """
     rng = np.random.default_rng(seed)
     D = bond_bounds(L, d, chi)
@@ -199,7 +202,8 @@ def turbulence_2d(L=10, chi=64, seed=2000, kmin=4.0, kmax=128.0):
 
     Stream-function modes with random phases on integer wavevectors kmin <= |k| <= kmax,
     per-mode |u_hat| ~ |k|^(-4/3) so the shell energy follows E(k) ~ k^(-5/3);
-    u = d(psi)/dy, v = -d(psi)/dx (so div u = 0); normalised to unit RMS; encoded with
+    u = d(psi)/dy, v = -d(psi)/dx (so div u = 0); both scaled by one factor so that
+    mean(u^2 + v^2) / 2 = 1 (a common factor keeps the field divergence-free); encoded with
     interleaved bits and compressed by TT-SVD to ``chi``.
     Returns (u_tt, v_tt, u_dense, v_dense).
     """
@@ -215,8 +219,9 @@ def turbulence_2d(L=10, chi=64, seed=2000, kmin=4.0, kmax=128.0):
     psi_hat = amp * np.exp(1j * phase)
     u = np.real(np.fft.ifft2(1j * ky * psi_hat))
     v = np.real(np.fft.ifft2(-1j * kx * psi_hat))
-    u /= np.sqrt(np.mean(u ** 2))
-    v /= np.sqrt(np.mean(v ** 2))
+    scale = np.sqrt(np.mean(u ** 2 + v ** 2) / 2.0)
+    u /= scale
+    v /= scale
     ut = tt_svd(interleave_2d(u, L), L, 4, chi)
     vt = tt_svd(interleave_2d(v, L), L, 4, chi)
     return ut, vt, u, v
