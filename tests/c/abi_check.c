@@ -1,6 +1,7 @@
 /* Plain C99 user of include/ttm.h: compiles against the header alone, links against
  * libttm.so, and exercises the calls that need no GPU (version, argument and option
  * validation, host-side output planning). */
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -49,6 +50,27 @@ int main(void) {
   CHECK(ttm_output_capacity(&A, &B, &opt) > 0);
   bA[0] = 2; /* boundary bond must be 1 */
   CHECK(ttm_output_capacity(&A, &B, &opt) < 0);
+
+  /* struct layout, compared with the ctypes mirror by the Python test */
+#define FIELD(T, f) printf("layout %s.%s %zu %zu\n", #T, #f, offsetof(T, f), sizeof(((T *)0)->f))
+  printf("layout ttm_tt.sizeof 0 %zu\n", sizeof(ttm_tt));
+  FIELD(ttm_tt, L); FIELD(ttm_tt, d); FIELD(ttm_tt, on_host); FIELD(ttm_tt, reserved);
+  FIELD(ttm_tt, bonds); FIELD(ttm_tt, cores);
+  printf("layout ttm_options.sizeof 0 %zu\n", sizeof(ttm_options));
+  FIELD(ttm_options, prec); FIELD(ttm_options, eps); FIELD(ttm_options, chi_max);
+  FIELD(ttm_options, chi_out); FIELD(ttm_options, max_sweeps); FIELD(ttm_options, use_graph);
+  FIELD(ttm_options, check_finite); FIELD(ttm_options, profile_kernels);
+  FIELD(ttm_options, f32_passes); FIELD(ttm_options, f32_block);
+  FIELD(ttm_options, polish_kept_dropped); FIELD(ttm_options, reserved1);
+  printf("layout ttm_report.sizeof 0 %zu\n", sizeof(ttm_report));
+  FIELD(ttm_report, status); FIELD(ttm_report, jacobi_sweeps_max); FIELD(ttm_report, max_bond);
+  FIELD(ttm_report, n_swaps); FIELD(ttm_report, n_contracts); FIELD(ttm_report, n_qr);
+  FIELD(ttm_report, discarded_weight); FIELD(ttm_report, err_bound); FIELD(ttm_report, norm_out);
+  FIELD(ttm_report, flops_counted); FIELD(ttm_report, seconds); FIELD(ttm_report, peak_workspace_bytes);
+  FIELD(ttm_report, bond_trace); FIELD(ttm_report, bond_trace_len); FIELD(ttm_report, n_kernel_launches);
+  FIELD(ttm_report, jacobi_launches); FIELD(ttm_report, jacobi_ms); FIELD(ttm_report, jacobi_flops);
+  FIELD(ttm_report, jacobi32_ms); FIELD(ttm_report, jacobi32_flops);
+#undef FIELD
 
   if (failures == 0) printf("c abi check ok\n");
   return failures == 0 ? 0 : 1;

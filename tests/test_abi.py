@@ -115,3 +115,22 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "c abi check ok" in r.stdout
+    # the ctypes mirrors in the binding have the header's layout, field by field
+    import ctypes
+    import paper_2410_19747_gb300.binding as b
+    mirrors = {"ttm_tt": b.c_tt, "ttm_options": b.c_options, "ttm_report": b.c_report}
+    seen = {k: set() for k in mirrors}
+    for line in r.stdout.splitlines():
+        if not line.startswith("layout "):
+            continue
+        _, name, off, size = line.split()
+        struct, field = name.split(".")
+        py = mirrors[struct]
+        if field == "sizeof":
+            assert ctypes.sizeof(py) == int(size), (struct, ctypes.sizeof(py), size)
+            continue
+        desc = getattr(py, field)
+        assert (desc.offset, desc.size) == (int(off), int(size)), (name, desc.offset, desc.size, off, size)
+        seen[struct].add(field)
+    for struct, py in mirrors.items():
+        assert seen[struct] == {f for f, _ in py._fields_}, struct
