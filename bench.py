@@ -37,22 +37,24 @@ L2_BYTES = 129 * 2 ** 20
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--chi", type=int, default=512)
     p.add_argument("--L", type=int, default=30)
     p.add_argument("--eps", type=float, default=1e-14)
-    p.add_argument("--prec", default="fp64")
+    p.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=1)
-    p.add_argument("--f32-passes", type=int, default=0, help="float32 preconditioning passes (0: default)")
+    p.add_argument("--f32-passes", type=int, default=0, help="float32 Jacobi passes (0: library default)")
+    p.add_argument("--newton-steps", type=int, default=0, help="float64 Newton steps (0: library default)")
+    p.add_argument("--split-digits", type=int, default=0, help="digits of bf16_split (0: library default)")
     p.add_argument("--batch", type=int, default=1,
                    help="independent products per step, multiplied in one ttm_multiply_batched call")
-    p.add_argument("--polish-kd", type=int, default=0, choices=[0, 1],
-                   help="1: float64 polish of the kept/dropped couplings only where the cap binds")
     p.add_argument("--f32-block", type=int, default=0, choices=[0, 8, 16],
                    help="block width of the float32 Jacobi (0: scalar kernel, the default)")
+    p.add_argument("--time-budget", type=float, default=1500.0,
+                   help="seconds of timed steps after which no further step is started")
     return p.parse_args()
 
 
@@ -64,14 +66,17 @@ def workload(L, chi, seed):
 
 
 def config(args):
+    prec = getattr(args, "prec", "fp64")
     return {"workload": "config3: random right-canonical TT pair, L=%d, d=2, chi=%d, a 1/k profile on every "
                         "bond (realised Schmidt spectra steeper), float64 cores, eps=%g, chi_max=chi_out=%d"
                         % (args.L, args.chi, args.eps, args.chi),
             "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
-            "precision_mode": args.prec, "batch": getattr(args, "batch", 1),
-            "svd": "one-sided Jacobi: %d float32 passes (%s) + float64 polish (%s)"
-                   % (args.f32_passes or 3, "block width %d" % args.f32_block if args.f32_block else "scalar",
-                      "kept/dropped pairs where the cap binds" if getattr(args, "polish_kd", 0) else "all pairs"),
+            "precision_mode": prec, "batch": getattr(args, "batch", 1),
+            "svd": "one-sided Jacobi, %d float32 passes (%s), then %d float64 Newton steps; GEMMs %s"
+                   % (args.f32_passes or 2, "block width %d" % args.f32_block if args.f32_block else "scalar",
+                      getattr(args, "newton_steps", 0) or 3,
+                      "on the float64 pipe" if prec == "fp64" else
+                      "as %d-digit bf16 products on the tensor cores" % (getattr(args, "split_digits", 0) or 8)),
             "l2": "flushed between timed steps (256 MiB write outside the timed events)"}
 
 
@@ -129,78 +134,160 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(args, flops_per_product, swap_flops_full, n_samples=2):
-    """The oracle's Swap (numpy/LAPACK float64) on full-size carriages, extrapolated to one
-    product by counted flops. Returns (products/s, seconds spent, description)."""
-    from oracle import ttm as ottm
-    rng = np.random.default_rng(7)
-    chi = args.chi
-    X = np.linalg.qr(rng.standard_normal((2 * chi, chi)))[0].reshape(chi, 2, chi)
-    Y = rng.standard_normal((chi, 2, chi)) / chi
-    t0 = time.perf_counter()
-    for _ in range(n_samples):
-        ottm.swap(X, Y, args.eps, chi)
-    dt = (time.perf_counter() - t0) / n_samples
-    per_product = dt * flops_per_product / swap_flops_full
-    return 1.0 / per_product, dt * n_samples, (
-        "%d full-size oracle Swaps (%dx2x%d carriages, numpy/LAPACK gesdd, %d host threads), "
-        "%.2f s each, extrapolated to one product by counted flops (%.3g / %.3g)"
-        % (n_samples, chi, chi, os.cpu_count(), dt, flops_per_product, swap_flops_full))
-
-
-def swap_model_flops(chi):
-    m = n = 2 * chi
-    return 2.0 * 4 * chi ** 3 + 2.0 * m * n * n + 2.0 * m * n * chi
-
-
-def model_flops(L, d, chi):
-    """Counted flops of one product from the schedule of Sec. II.B with every bond at its
-    upper bound min(d^i, d^(L-i), chi) (the same counting formulas the library applies
-    to the realised bonds). Used only by the reference arm, which runs no GPU code."""
-    ub = lambda i, n: min(chi, d ** min(i, n - i))
+def schedule_flops(bondsA, bondsB, d, chi_max):
+    """Counted flops of one product (the model of Sec. II.B's schedule: Theta, SVD-equivalent
+    Gram + U formation, Contract, Householder QR + R merge; Jacobi/Newton iterations
+    excluded) with every bond at the upper bound the library's planner assigns it:
+    min(d D_l, D_r) after a QR move, min(d D_l, d D_r, chi_max) after a Swap. When the caps
+    bind (the metric's configuration) these are the realised bonds, and the count equals the
+    report's flops_counted; the formulas are the library's."""
+    L = len(bondsA) - 1
+    bA, bB = list(bondsA), list(bondsB)
     fl = 0.0
 
-    def qr(m, n, k, rr):
+    def qr(dl, dr, drr):
+        m, n = d * dl, dr
+        k = min(m, n)
         p, q = max(m, n), min(m, n)
-        return 2 * p * q * q - 2 / 3 * q ** 3 + 2 * m * k * k - 2 / 3 * k ** 3 + 2 * k * n * d * rr
+        return k, 2 * p * q * q - 2 / 3 * q ** 3 + 2 * m * k * k - 2 / 3 * k ** 3 + 2 * k * n * d * drr
 
-    # preparation: two left-canonicalising QR sweeps
-    for _ in range(2):
+    for b in (bA, bB):                       # a1: both trains left-canonical
         for k in range(L - 1):
-            Dl, Dr, Drr = ub(k, L), ub(k + 1, L), ub(k + 2, L)
-            fl += qr(d * Dl, Dr, min(d * Dl, Dr), Drr)
-    # sweep: iteration i moves the centre through Pi_{i+1}..Pi_N and swaps back
+            nb, f = qr(b[k], b[k + 1], b[k + 2])
+            fl += f
+            b[k + 1] = nb
+    mtL = [bB[L - j] for j in range(L)]      # Eq. tensor: B reversed, bond legs exchanged
+    mtR = [bB[L - 1 - j] for j in range(L)]
+    piL, piR = [0] * (L + 2), [0] * (L + 2)
+    fl += 2 * d * bA[L - 1] * bA[L] * mtR[0]  # a2
+    piL[L], piR[L] = bA[L - 1], mtR[0]
     for i in range(L - 1, 0, -1):
-        for j in range(i + 1, L + 1):
-            fl += qr(d * chi, chi, chi, chi)
-        for j in range(L, i, -1):
-            Dl = Dm = Dr = chi
-            m = n = d * chi
-            fl += 2.0 * d * d * Dl * Dm * Dr + 2.0 * m * n * n + 2.0 * m * n * chi
-        fl += 2.0 * d * chi ** 3
+        mvR = mtR[L - i]
+        for j in range(i + 1, L + 1):        # a3
+            nxt = piR[j + 1] if j < L else mvR
+            nb, f = qr(piL[j], piR[j], nxt)
+            fl += f
+            piR[j] = nb
+            if j < L:
+                piL[j + 1] = nb
+        for j in range(L, i, -1):            # a4 + a5
+            Dl, Dm, Dr = piL[j], piR[j], mvR
+            nb = min(d * Dl, d * Dr)
+            if chi_max > 0:
+                nb = min(nb, chi_max)
+            m, n = d * Dl, d * Dr
+            fl += 2.0 * d * d * Dl * Dm * Dr + 2.0 * m * n * n + 2.0 * m * n * nb
+            piL[j], piR[j], mvR = nb, mvR, nb
+        fl += 2.0 * d * bA[i - 1] * bA[i] * mvR  # a6
+        piL[i], piR[i] = bA[i - 1], mvR
     return fl
 
 
+def swap_model_flops(Dl, Dm, Dr, d, k):
+    m, n = d * Dl, d * Dr
+    return 2.0 * d * d * Dl * Dm * Dr + 2.0 * m * n * n + 2.0 * m * n * k
+
+
+def sample_carriages(args, A, B):
+    """A full-size Swap of the benchmark workload: the carriage of A at the middle site made
+    left-orthonormal (as the sweep holds it) and the middle carriage of the reversed B
+    (bond legs exchanged, Eq. tensor) as the mover."""
+    from oracle import tt as ott
+    K = ott.left_canonical(A)
+    Mc = ott.left_canonical(B)
+    mid = len(A) // 2
+    X = K[mid]
+    Y = Mc[mid].transpose(2, 1, 0).copy()
+    return X, Y
+
+
+_SINGLE_CORE = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import ttm as ottm
+d = np.load(%r)
+X, Y = d["X"], d["Y"]
+ottm.swap(X, Y, %r, %d)
+t0 = time.perf_counter()
+for _ in range(%d):
+    ottm.swap(X, Y, %r, %d)
+print(json.dumps({"dt": (time.perf_counter() - t0) / %d}))
+"""
+
+
+def time_oracle_swap(X, Y, eps, cap, n, threads):
+    """Seconds per call of the oracle's Swap on (X, Y): in this process (all host threads of
+    the BLAS) or, for threads == 1, in a child process started with one BLAS thread."""
+    from oracle import ttm as ottm
+    if threads != 1:
+        ottm.swap(X, Y, eps, cap)
+        t0 = time.perf_counter()
+        for _ in range(n):
+            ottm.swap(X, Y, eps, cap)
+        return (time.perf_counter() - t0) / n
+    import tempfile
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "xy.npz")
+        np.savez(path, X=X, Y=Y)
+        code = _SINGLE_CORE % (ROOT, path, eps, cap, n, eps, cap, n)
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        if out.returncode != 0:
+            raise RuntimeError(out.stderr[-500:])
+        return json.loads(out.stdout.strip().splitlines()[-1])["dt"]
+
+
+def cpu_baseline(args, A, B, flops_product, n_multi=3, n_single=1):
+    """The CPU float64 oracle timed on a bounded sample of the workload: full-size Swaps
+    (oracle.ttm.swap: tensordot + LAPACK gesdd) on carriages of the benchmark inputs,
+    extrapolated to one product by the counted flops of the product's schedule. Returns
+    (products/s on all host threads, products/s on one core, description, seconds spent)."""
+    t_start = time.perf_counter()
+    X, Y = sample_carriages(args, A, B)
+    f_swap = swap_model_flops(X.shape[0], X.shape[2], Y.shape[2], X.shape[1], args.chi)
+    cores = os.cpu_count()
+    dt_multi = time_oracle_swap(X, Y, args.eps, args.chi, n_multi, cores)
+    try:
+        dt_single = time_oracle_swap(X, Y, args.eps, args.chi, n_single, 1)
+    except Exception:  # the single-core figure is context; the multi-thread one is the baseline
+        dt_single = None
+    per_product = dt_multi * flops_product / f_swap
+    desc = ("%d full-size Swaps of the workload (oracle.ttm.swap on the left-orthonormal middle carriage "
+            "of A and the middle carriage of the reversed B, %dx%dx%d and %dx%dx%d; numpy tensordot + "
+            "LAPACK gesdd), %.3f s each on %d host threads%s; extrapolated to one product by counted flops "
+            "(%.4g per product / %.4g per Swap)"
+            % (n_multi, X.shape[0], X.shape[1], X.shape[2], Y.shape[0], Y.shape[1], Y.shape[2], dt_multi, cores,
+               (", %.3f s on 1 core" % dt_single) if dt_single else "", flops_product, f_swap))
+    single = (1.0 / (dt_single * flops_product / f_swap)) if dt_single else None
+    return 1.0 / per_product, single, desc, time.perf_counter() - t_start
+
+
 def run_reference(args, rank):
-    """Reference arm: the CPU float64 oracle (the only implementation of the paper here)."""
+    """Reference arm: the CPU float64 oracle (the only other implementation of the paper
+    here), on the bounded sample of cpu_baseline per step."""
     if rank != 0:
         return
-    flops_product = model_flops(args.L, 2, args.chi)
+    A, B = workload(args.L, args.chi, rank_seed(0))
+    flops_product = schedule_flops([1] + [c.shape[2] for c in A], [1] + [c.shape[2] for c in B], 2, args.chi)
     for _ in range(args.warmup):
-        cpu_baseline(args, flops_product, swap_model_flops(args.chi), n_samples=1)
-    vals, spent = [], 0.0
-    desc = ""
+        cpu_baseline(args, A, B, flops_product, n_multi=1, n_single=0)
+    vals, desc = [], ""
+    spent = 0.0
     for _ in range(args.steps):
-        v, s, desc = cpu_baseline(args, flops_product, swap_model_flops(args.chi), n_samples=1)
+        v, _, desc, dt = cpu_baseline(args, A, B, flops_product, n_multi=1, n_single=0)
         vals.append(v)
-        spent += s
+        spent += dt
     value = float(np.mean(vals))
+    _, single, _, _ = cpu_baseline(args, A, B, flops_product, n_multi=1, n_single=1)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "sample_s_per_step": spent / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args),
             "cpu_baseline": {"value": value, "unit": "products/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc, "value_1core": single},
             "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -221,25 +308,59 @@ def max_over_ranks(dist, x, device):
     return float(t.item())
 
 
-def jacobi_roofline(reps, t_local):
-    """Roofline object of the dominant one-sided Jacobi kernel of the timed steps (device
-    time from CUDA events on the library's stream, flops counted on the device), with the
-    other Jacobi kernel attached under "other_kernels"."""
+def measured_peaks():
+    """The machine's measured peaks (generated MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"bf16_tflops": float(d["bf16_tflops"]), "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_roofline(args, reps, t_local):
+    """Roofline object of the dominant kernel family of the timed steps (device time from CUDA
+    events on the library's stream, summed over the launches of the family): the GEMMs
+    (float64 pipe, or the tensor cores for bf16_split: digit products = S (S + 1) / 2 bf16
+    GEMMs per algorithmic GEMM), the float32 one-sided Jacobi passes (flops counted on the
+    device) or the Householder QR. The other families follow under "other_kernels"."""
+    peaks = measured_peaks()
+    S = getattr(args, "split_digits", 0) or 8
+    tc = getattr(args, "prec", "fp64") == "bf16_split"
     kernels = []
-    n_sw = sum(r["n_swaps"] for r in reps)
-    for name, ms_key, fl_key, peak, src, n_l in (
-            ("hestenes_kernel<double> (one-sided Jacobi polish, float64)", "jacobi_ms", "jacobi_flops",
-             FP64_PEAK_TFLOPS, "nominal float64 rate: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz", n_sw),
-            ("hestenes_kernel<float> (one-sided Jacobi preconditioning passes, float32)", "jacobi32_ms",
-             "jacobi32_flops", FP32_PEAK_TFLOPS, "nominal float32 rate: 128 FFMA/clk/SM x 152 SMs x 2.07 GHz",
-             sum(r["jacobi_launches"] for r in reps) - n_sw)):
-        ms = sum(r[ms_key] for r in reps)
-        fl = sum(r[fl_key] for r in reps)
-        ach = (fl / (ms / 1e3) / 1e12) if ms > 0 else None
-        kernels.append({"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                        "peak_source": src, "frac": (ach / peak) if ach else None, "traffic": None,
-                        "share_of_step": ms / 1e3 / t_local if t_local > 0 else None,
-                        "launches": n_l, "avg_launch_ms": ms / max(1, n_l)})
+    gemm_ms = sum(r["gemm_ms"] for r in reps)
+    gemm_fl = sum(r["gemm_flops"] for r in reps)
+    n_g = sum(r["gemm_launches"] for r in reps)
+    if tc:
+        ach = gemm_fl * S * (S + 1) / 2 / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+        kernels.append({"bound": "tensor", "kernel": "oz_gemm_kernel (+ exponent and digit kernels): float64 "
+                        "GEMMs as %d-digit bf16 tcgen05 products" % S, "achieved": ach,
+                        "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                        "peak_source": "%s dense bf16, sustained (kernel timed inside a long step)" % peaks["source"],
+                        "fp64_equivalent_tflops": (gemm_fl / (gemm_ms / 1e3) / 1e12) if gemm_ms > 0 else None,
+                        "ms": gemm_ms, "launches": n_g})
+    else:
+        ach = gemm_fl / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+        kernels.append({"bound": "alu", "kernel": "dgemm_kernel (float64 DFMA)", "achieved": ach,
+                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "peak_source": "nominal float64 rate, 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (a torch/cuBLAS "
+                                       "DGEMM probe of this pool reached 1.10)",
+                        "ms": gemm_ms, "launches": n_g})
+    j_ms = sum(r["jacobi32_ms"] for r in reps)
+    j_fl = sum(r["jacobi32_flops"] for r in reps)
+    kernels.append({"bound": "alu", "kernel": "hestenes_kernel<float> (one-sided Jacobi, float32)",
+                    "achieved": (j_fl / (j_ms / 1e3) / 1e12) if j_ms > 0 else None, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "nominal float32 rate, 128 FFMA/clk/SM x 152 SMs x 2.07 GHz "
+                                                      "(a torch SGEMM probe of this pool reached 69.8)",
+                    "ms": j_ms, "launches": sum(r["jacobi_launches"] for r in reps)})
+    kernels.append({"bound": "latency", "kernel": "householder_kernel (float64 QR of the gauge moves)",
+                    "achieved": None, "peak": None, "unit": None, "ms": sum(r["qr_ms"] for r in reps),
+                    "launches": None})
+    for k in kernels:
+        k["frac"] = (k["achieved"] / k["peak"]) if (k["achieved"] and k["peak"]) else None
+        k["share_of_step"] = k["ms"] / 1e3 / t_local if t_local > 0 else None
+        k["traffic"] = None
     kernels.sort(key=lambda k: -(k["share_of_step"] or 0.0))
     roof = dict(kernels[0])
     roof["other_kernels"] = kernels[1:]
@@ -251,20 +372,21 @@ def make_line(args, reps, t_local, t, world, e2e, clocks):
     report per step (launch-wide figures: a batched step shares its launches).
     t_local: this rank's summed step time; t: the max over ranks."""
     r0 = reps[-1]
-    products = world * args.steps * getattr(args, "batch", 1)
+    products = world * len(reps) * getattr(args, "batch", 1)
     flops = float(np.mean([r["flops_counted"] for r in reps]))
     return {
-        "metric": METRIC, "value": products / t, "unit": "products/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": products / t, "unit": "products/s", "n_gpus": world, "steps": len(reps),
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / len(reps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config(args),
         "tflops_counted": flops * products / t / 1e12,
-        "roofline": jacobi_roofline(reps, t_local),
+        "roofline": kernel_roofline(args, reps, t_local),
         "e2e": e2e,
         "gpu_launches": int(sum(r["n_kernel_launches"] for r in reps)),
         "clocks": clocks,
         "report": {k: r0[k] for k in ("n_swaps", "n_contracts", "n_qr", "max_bond", "discarded_weight",
-                                      "err_bound", "norm_out", "jacobi_sweeps_max")},
+                                      "err_bound", "norm_out", "jacobi_sweeps_max", "newton_residual",
+                                      "n_nonconverged", "status", "flops_counted")},
     }
 
 
@@ -292,7 +414,7 @@ def main():
              for a, b in host_pairs]
     Ag, Bg = pairs[0]
     kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec, f32_passes=args.f32_passes,
-              f32_block=args.f32_block, polish_kept_dropped=args.polish_kd)
+              f32_block=args.f32_block, newton_steps=args.newton_steps, split_digits=args.split_digits)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -310,8 +432,15 @@ def main():
     torch.cuda.synchronize(dev)
 
     reps, dts = [], []
+    stopped = False
     with ClockSampler(dev.index) as clk:
-        for _ in range(args.steps):
+        for q in range(args.steps):
+            # no step is started that would end past the budget (the ranks agree on the decision)
+            if q > 0:
+                proj = max_over_ranks(dist, sum(dts) + sum(dts) / len(dts), dev)
+                if proj > args.time_budget:
+                    stopped = True
+                    break
             flush.fill_(1.0)                       # L2 flush, outside the timed events
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -352,11 +481,15 @@ def main():
                          {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d,
                           "d2h_bytes_per_step": d2h, **({"error": e2e_err} if e2e_err else {})},
                          clk.summary())
+        if stopped:
+            line["steps_requested"] = args.steps
+            line["stopped_early"] = "the next step would have ended after --time-budget %.0f s" % args.time_budget
         flops = float(np.mean([r["flops_counted"] for r in reps]))
         if not args.no_cpu_baseline:
-            v, spent, desc = cpu_baseline(args, flops, swap_model_flops(args.chi))
+            A, B = host_pairs[0]
+            v, v1, desc, spent = cpu_baseline(args, A, B, flops)
             line["cpu_baseline"] = {"value": v, "unit": "products/s", "cores": os.cpu_count(), "kind": "oracle",
-                                    "sample": desc}
+                                    "sample": desc, "value_1core": v1, "sample_s": spent}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -45,19 +45,25 @@ typedef enum {
   TTM_ERR_CUDA = -6,        /* a CUDA runtime call failed (message has the cause)    */
   TTM_ERR_TIMEOUT = -7,     /* a bounded device-side loop hit its iteration limit    */
   TTM_ERR_RANK_CAP = -8,    /* a bond would exceed the library's supported maximum   */
-  TTM_ERR_UNSUPPORTED = -9  /* option combination not supported                      */
+  TTM_ERR_UNSUPPORTED = -9, /* option combination not supported                      */
+  TTM_WARN_NOT_CONVERGED = 1 /* the product was formed, but at least one Swap SVD did not
+                               converge (its float64 Jacobi hit the sweep limit): the
+                               report's n_nonconverged counts them; the truncation may be
+                               suboptimal there                                       */
 } ttm_status;
 
-/* Arithmetic of the GEMM-shaped contractions. Decompositions (QR, SVD) and norms
- * always run in float64 on the GPU. */
+/* Arithmetic of the GEMM-shaped work: the contractions (Theta of every Swap, Contract, the
+ * R merge of every gauge move) and the GEMMs inside the Swap SVD (its Newton steps). The
+ * Householder QR, the Jacobi rotations, norms and the truncation rule always run on the
+ * CUDA cores (float32 Jacobi passes, everything else float64). */
 typedef enum {
-  TTM_PREC_FP64 = 0,       /* plain float64 everywhere (the reference form): the Swap SVD
-                              is polished in float64 until its one-sided Jacobi converges */
-  TTM_PREC_TF32X3 = 1,     /* tensor-core split products: not built (TTM_ERR_UNSUPPORTED) */
-  TTM_PREC_BF16X3 = 2,     /* tensor-core split products: not built (TTM_ERR_UNSUPPORTED) */
-  TTM_PREC_MIXED_F32 = 3   /* the SVD rotation is found in float32 and polished by at most
-                              max_sweeps (default 3) float64 sweeps; the factorisation
-                              W V^T = Theta, the GEMMs, QR and norms stay float64          */
+  TTM_PREC_FP64 = 0,       /* every GEMM on the float64 pipe (the reference form)         */
+  TTM_PREC_BF16_SPLIT = 2  /* every GEMM on the tcgen05 tensor cores as the exactly sliced
+                              product of bf16 digits (Ozaki scheme): each float64 operand
+                              row (column) is scaled by a power of two and split into
+                              split_digits digits of 7 bits; the digit products are summed
+                              exactly in float32 and combined in float64. 8 digits (the
+                              default) give float64 accuracy                             */
 } ttm_precision;
 
 typedef enum {
@@ -84,31 +90,28 @@ typedef struct {
                                (or chi_max = 0) a final TT-SVD rounding truncates bonds
                                1..L-1 in order with this cap and the eps rule, leaving the
                                norm on the last core (built; not yet run on a GPU)        */
-  int32_t max_sweeps;       /* one-sided Jacobi sweep limit per SVD; 0 = library default */
-  int32_t use_graph;        /* reserved for CUDA-graph capture of the sweep: not built,
-                               must be 0 (1 returns TTM_ERR_UNSUPPORTED)                 */
-  int32_t check_finite;     /* reserved for a device scan of the inputs for NaN/Inf: not
-                               built, must be 0 (1 returns TTM_ERR_UNSUPPORTED)          */
-  int32_t profile_kernels;  /* 1: time every one-sided Jacobi launch with CUDA events on
-                               the handle's stream (fills the jacobi_* report fields)      */
-  int32_t f32_passes;       /* float32 preconditioning passes of every Swap SVD before the
-                               float64 polish: 0 = library default (3), 1..8 accepted     */
+  int32_t max_sweeps;       /* sweep limit of the float32 Jacobi passes after the first;
+                               0 = 30                                                     */
+  int32_t use_graph;        /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
+  int32_t check_finite;     /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
+  int32_t profile_kernels;  /* 1: time every GEMM, float32 Jacobi and Householder launch
+                               with CUDA events on the handle's stream (fills gemm_ms,
+                               jacobi32_ms and qr_ms of the report)                      */
+  int32_t f32_passes;       /* float32 one-sided Jacobi passes of every Swap SVD: 0 = 2
+                               (the first stops after 3 sweeps), 1..8 accepted           */
   int32_t f32_block;        /* float32 passes: 0 = scalar one-sided Jacobi (one grid
-                               barrier per round of column pairs, default); 8 or 16 =
-                               block Jacobi on blocks of that many columns (one barrier per
-                               round of block pairs; experimental, not yet run on a GPU)  */
-  int32_t polish_kept_dropped; /* 1: when the cap clearly binds a Swap (Eq. eps rank above
-                               the cap by a margin), polish in float64 only the couplings
-                               between kept and dropped columns, which alone decide the
-                               truncated tensor and the discarded weight; 0 (default):
-                               polish all pairs (experimental, not yet run on a GPU)     */
-  int32_t reserved1;        /* must be 0                                                 */
+                               barrier per round of column pairs); 8 or 16 = block Jacobi
+                               on blocks of that many columns (one barrier per round of
+                               block pairs)                                              */
+  int32_t newton_steps;     /* float64 Newton steps that finish every Swap SVD after the
+                               float32 passes: 0 = 3, 1..8 accepted                      */
+  int32_t split_digits;     /* digits per operand of TTM_PREC_BF16_SPLIT: 0 = 8, 2..8   */
 } ttm_options;
 
 /* Filled by ttm_multiply. All fields are host values once the call returns. */
 typedef struct {
-  int32_t status;
-  int32_t jacobi_sweeps_max;   /* largest sweep count any SVD needed                     */
+  int32_t status;              /* TTM_OK or TTM_WARN_NOT_CONVERGED                        */
+  int32_t jacobi_sweeps_max;   /* largest sweep count of any float32 Jacobi pass          */
   int64_t max_bond;            /* largest bond created by any Swap / QR / Contract       */
   int64_t n_swaps, n_contracts, n_qr;
   double discarded_weight;     /* sum_j w_j, w_j = sum of dropped lambda^2 of truncation j */
@@ -121,13 +124,26 @@ typedef struct {
   int64_t *bond_trace;         /* caller array or NULL: max chain bond after each Contract */
   int64_t bond_trace_len;      /* in: capacity of bond_trace; out: entries written (N)    */
   int64_t n_kernel_launches;   /* kernels this call launched (all products of a batch)   */
-  int64_t jacobi_launches;     /* one-sided Jacobi launches                               */
-  double jacobi_ms;            /* their summed device time (profile_kernels = 1), else 0 */
-  double jacobi_flops;         /* float64 flops the polish kernels executed (counted on
-                                  the device: dot products and applied rotations)         */
-  double jacobi32_ms;          /* device time of the float32 preconditioning passes
+  int64_t jacobi_launches;     /* float32 one-sided Jacobi launches                       */
+  double gemm_ms;              /* device time of every GEMM-shaped launch, for a
+                                  tensor-core GEMM its exponent and digit kernels included
+                                  (profile_kernels = 1), else 0                            */
+  double newton_residual;      /* largest max(|S_ij|, |E_ij| / 2) of the last Newton step
+                                  of any SVD (see ttm_newton.cuh); float64 rounding level
+                                  when every SVD converged                                 */
+  double jacobi32_ms;          /* device time of the float32 Jacobi passes
                                   (profile_kernels = 1), else 0                           */
-  double jacobi32_flops;       /* float32 flops those passes executed                      */
+  double jacobi32_flops;       /* float32 flops those passes executed (launch-wide)       */
+  int64_t n_nonconverged;      /* SVDs that did not converge (see TTM_WARN_NOT_CONVERGED) */
+  int64_t n_frozen_pairs;      /* column pairs the last Newton steps left unrotated as
+                                  degenerate relative to their coupling                    */
+  double gemm_flops;           /* algorithmic flops of those GEMMs from the realised bonds
+                                  (2 M N K; M (M + 1) K for a symmetric Gram), launch-wide */
+  int64_t gemm_launches;       /* GEMMs of the call (launch-wide)                          */
+  double qr_ms;                /* device time of the Householder QR launches
+                                  (profile_kernels = 1), else 0                            */
+  int64_t n_fallback;          /* Swap SVDs whose Newton steps did not reach float64
+                                  rounding and were finished by the float64 Jacobi        */
 } ttm_report;
 
 /* Creates a handle bound to CUDA device `device` and stream `cuda_stream`
@@ -213,6 +229,16 @@ ttm_status ttm_inner3(ttm_handle *h, const ttm_tt *W, const ttm_tt *A, const ttm
 #define TTM_NOALLOC_SCRATCH_BYTES (16u << 20)
 ttm_status ttm_multiply_noalloc(const ttm_tt *A, const ttm_tt *B, ttm_tt *out, const ttm_options *opt,
                                 void *cuda_stream);
+
+/*
+ * C = A B for float64 device matrices in column-major order (A: M x K with leading dimension
+ * lda >= M, B: K x N with ldb >= K, C: M x N with ldc >= M; 1 <= M, N, K <= 2^20), on the
+ * handle's stream, with the GEMM kernels of the product: prec = TTM_PREC_FP64 runs the float64
+ * kernel, TTM_PREC_BF16_SPLIT the tensor-core digit product (split_digits of the handle's
+ * options). Blocks until C is written. The workspace of the digits is handle-owned.
+ */
+ttm_status ttm_gemm(ttm_handle *h, ttm_precision prec, int64_t M, int64_t N, int64_t K, const double *A,
+                    int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc);
 
 /* Waits for all work queued on the handle's stream. */
 ttm_status ttm_synchronize(ttm_handle *h);

@@ -8,7 +8,7 @@ the in-tree build (``_build.py``) and the ctypes binding (``binding.py``).
 
 from .binding import (  # noqa: F401
     EXPORTED, Handle, TTMError, load_library, library_path, output_capacity,
-    ttm_backward, ttm_inner, ttm_inner3, ttm_multiply, ttm_multiply_batched,
+    ttm_backward, ttm_gemm, ttm_inner, ttm_inner3, ttm_multiply, ttm_multiply_batched,
 )
 from ._build import build  # noqa: F401
 from .autograd import TTMProductLoss, product_loss  # noqa: F401

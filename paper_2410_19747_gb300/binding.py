@@ -14,16 +14,16 @@ import numpy as np
 from . import _build
 
 TTM_OK = 0
-PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "mixed": 3}
+PREC = {"fp64": 0, "bf16_split": 2}
 LOSS = {"inner": 0, "sqdist": 1}
-STATUS = {0: "TTM_OK", -1: "TTM_ERR_INVALID_ARG", -2: "TTM_ERR_SHAPE", -3: "TTM_ERR_NOMEM",
+STATUS = {0: "TTM_OK", 1: "TTM_WARN_NOT_CONVERGED", -1: "TTM_ERR_INVALID_ARG", -2: "TTM_ERR_SHAPE", -3: "TTM_ERR_NOMEM",
           -4: "TTM_ERR_WORKSPACE", -5: "TTM_ERR_NONFINITE", -6: "TTM_ERR_CUDA",
           -7: "TTM_ERR_TIMEOUT", -8: "TTM_ERR_RANK_CAP", -9: "TTM_ERR_UNSUPPORTED"}
 
 # Every symbol include/ttm.h declares (checked by the CPU test suite).
 EXPORTED = ["ttm_create", "ttm_destroy", "ttm_set_options", "ttm_multiply", "ttm_multiply_batched",
             "ttm_output_capacity", "ttm_backward", "ttm_inner", "ttm_inner3", "ttm_synchronize",
-            "ttm_tt_free", "ttm_last_error", "ttm_version", "ttm_multiply_noalloc"]
+            "ttm_tt_free", "ttm_last_error", "ttm_version", "ttm_multiply_noalloc", "ttm_gemm"]
 
 
 class TTMError(RuntimeError):
@@ -43,7 +43,7 @@ class c_options(ctypes.Structure):
                 ("chi_out", ctypes.c_int64), ("max_sweeps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("check_finite", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
                 ("f32_passes", ctypes.c_int32), ("f32_block", ctypes.c_int32),
-                ("polish_kept_dropped", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("newton_steps", ctypes.c_int32), ("split_digits", ctypes.c_int32)]
 
 
 class c_report(ctypes.Structure):
@@ -53,9 +53,11 @@ class c_report(ctypes.Structure):
                 ("norm_out", ctypes.c_double), ("flops_counted", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("peak_workspace_bytes", ctypes.c_int64), ("bond_trace", ctypes.POINTER(ctypes.c_int64)),
                 ("bond_trace_len", ctypes.c_int64), ("n_kernel_launches", ctypes.c_int64),
-                ("jacobi_launches", ctypes.c_int64), ("jacobi_ms", ctypes.c_double),
-                ("jacobi_flops", ctypes.c_double), ("jacobi32_ms", ctypes.c_double),
-                ("jacobi32_flops", ctypes.c_double)]
+                ("jacobi_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
+                ("newton_residual", ctypes.c_double), ("jacobi32_ms", ctypes.c_double),
+                ("jacobi32_flops", ctypes.c_double), ("n_nonconverged", ctypes.c_int64),
+                ("n_frozen_pairs", ctypes.c_int64), ("gemm_flops", ctypes.c_double),
+                ("gemm_launches", ctypes.c_int64), ("qr_ms", ctypes.c_double), ("n_fallback", ctypes.c_int64)]
 
 
 _LIB = None
@@ -89,6 +91,10 @@ def load_library(build_if_missing=False):
     lib.ttm_inner3.argtypes = [ctypes.c_void_p, P(c_tt), P(c_tt), P(c_tt), P(ctypes.c_double)]
     lib.ttm_multiply_noalloc.argtypes = [P(c_tt), P(c_tt), P(c_tt), P(c_options), ctypes.c_void_p]
     lib.ttm_multiply_noalloc.restype = ctypes.c_int
+    lib.ttm_gemm.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_int64]
+    lib.ttm_gemm.restype = ctypes.c_int
     lib.ttm_synchronize.argtypes = [ctypes.c_void_p]
     lib.ttm_tt_free.argtypes = [ctypes.c_void_p, P(c_tt)]
     lib.ttm_last_error.restype = ctypes.c_char_p
@@ -101,15 +107,18 @@ def load_library(build_if_missing=False):
 
 
 def _check(status):
-    if status != TTM_OK:
+    """Raises on an error status; a warning status (positive) is returned to the caller, and
+    the report of the call carries the details."""
+    if status < TTM_OK:
         raise TTMError(status, _LIB.ttm_last_error().decode())
+    return status
 
 
 def make_options(prec="fp64", eps=0.0, chi_max=0, chi_out=0, max_sweeps=0, use_graph=0, profile=0,
-                 f32_passes=0, f32_block=0, polish_kept_dropped=0):
+                 f32_passes=0, f32_block=0, newton_steps=0, split_digits=0):
     return c_options(PREC[prec] if isinstance(prec, str) else int(prec), float(eps), int(chi_max),
                      int(chi_out), int(max_sweeps), int(use_graph), 0, int(profile), int(f32_passes),
-                     int(f32_block), int(polish_kept_dropped), 0)
+                     int(f32_block), int(newton_steps), int(split_digits))
 
 
 class TTDesc:
@@ -219,12 +228,12 @@ def _shape_out(o, bufs, d):
 
 
 def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                         f32_passes=0, f32_block=0, polish_kept_dropped=0):
+                         f32_passes=0, f32_block=0, newton_steps=0, split_digits=0):
     """[(A_i, B_i)] -> ([Omega_i], [report_i]) with one batched launch sequence (ttm_multiply_batched)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
                        profile=profile, f32_passes=f32_passes, f32_block=f32_block,
-                       polish_kept_dropped=polish_kept_dropped)
+                       newton_steps=newton_steps, split_digits=split_digits)
     n = len(pairs)
     da = [TTDesc(A) for A, _ in pairs]
     db = [TTDesc(B) for _, B in pairs]
@@ -252,12 +261,12 @@ def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp6
 
 
 def ttm_multiply(handle, A, B, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                 f32_passes=0, f32_block=0, polish_kept_dropped=0):
+                 f32_passes=0, f32_block=0, newton_steps=0, split_digits=0):
     """Omega = A o B through ttm_multiply. Returns (cores, report)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
                        profile=profile, f32_passes=f32_passes, f32_block=f32_block,
-                       polish_kept_dropped=polish_kept_dropped)
+                       newton_steps=newton_steps, split_digits=split_digits)
     a, b = TTDesc(A), TTDesc(B)
     o = make_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out)
     cap = int(lib.ttm_output_capacity(ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(o)))
@@ -301,3 +310,19 @@ def ttm_backward(handle, kind, A, B, WC, want_a=True, want_b=True):
                                    ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(w.c), ctypes.byref(v),
                                    ctypes.byref(ga.c) if ga else None, ctypes.byref(gb.c) if gb else None))
     return v.value, gA, gB
+
+
+def ttm_gemm(handle, A, B, prec="fp64"):
+    """C = A B through ttm_gemm for 2-D float64 CUDA tensors (any strides with a unit row
+    stride are passed as column-major views; other layouts are made contiguous first)."""
+    import torch
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    a = A.t().contiguous().t() if A.stride(0) != 1 else A     # column-major views
+    b = B.t().contiguous().t() if B.stride(0) != 1 else B
+    C = torch.empty((N, M), dtype=torch.float64, device=A.device).t()
+    _check(handle.lib.ttm_gemm(handle.h, PREC[prec] if isinstance(prec, str) else int(prec), M, N, K,
+                               a.data_ptr(), max(a.stride(1), M), b.data_ptr(), max(b.stride(1), K),
+                               C.data_ptr(), M))
+    return C

@@ -61,9 +61,10 @@ void Engine::qr_move(int c, int& nx, int bl, int& br, int brr) {
     const Dim m{d_, bl}, n{1, br};
     copy2d(RowToColFn{tab_, c, ws(WS_T), m, n}, 1, m_ub, n_ub);
     QRArgs qa{tab_, ws(WS_T), ws(WS_TAU), ws(WS_R), ws(WS_Q), m, n, nbnd, n_ub, k_ub};
-    coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8);
+    timed(2, [&] { coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8); });
     copy2d(ColToRowFn{tab_, ws(WS_Q), c, m, Dim{1, nbnd}}, 1, m_ub, k_ub);
-    gemm(RMergeFn{tab_, ws(WS_R), nx, out, nbnd, br, brr, d_}, 1, k_ub, d_ * umax(brr));
+    gemm(RMergeFn{tab_, ws(WS_R), nx, out, nbnd, br, brr, d_}, 1, k_ub, d_ * umax(brr), n_ub,
+         GemmShape{Dim{1, nbnd}, Dim{d_, brr}, Dim{1, br}, 1, 0});
   }
   put_buf(nx);
   nx = out;
@@ -85,7 +86,6 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
   }
   const int nbnd = new_bond(kub);
   const int m_ub = d_ * umax(bl), n_ub = d_ * umax(br), k_ub = umax(nbnd);
-  const int nscr = new_bond(std::vector<int>(Z_, n_ub));  // receives n from the V orthonormalisation
   t_elems_ = std::max(t_elems_, (long)m_ub * n_ub);
   v_elems_ = std::max(v_elems_, (long)n_ub * n_ub);
   x_elems_ = std::max(x_elems_, (long)std::max(m_ub, n_ub) * n_ub);
@@ -95,97 +95,109 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
   note_carriage(bl, nbnd);
   note_carriage(nbnd, br);
   const int wslot = ST_NFIXED + n_trunc_++;
-  // kept/dropped polish: bond ids of the provisional rank (after the cap) and the Eq. eps rank
-  const bool kd = opt_.polish_kept_dropped != 0 && kind == SK_SWAP && cap > 0;
-  const int nprov = kd ? new_bond(kub) : -1;
-  const int nepsr = kd ? new_bond(std::vector<int>(Z_, n_ub)) : -1;
   const int npass = f32_passes();
   const int sw32 = jac_launch_;
   jac_launch_ += npass;
-  const int sw64 = jac_launch_++;
+  const int sw64 = jac_launch_++;          // the fallback's float64 Jacobi
+  const int nprov = new_bond(kub);         // provisional rank before the Newton steps
   if (launch_) {
     const Dim m{d_, bl}, n{d_, br};
     const int npad_ub = n_ub + (n_ub & 1);
     const long pairs = (long)Z_ * (npad_ub / 2);
     // 1. Theta = X Y with the physical legs permuted, column-major m x n (Fig. 1C)
     gemm(ThetaFn{tab_, x, y, ws(WS_T), bl, bm, br, d_, kind == SK_ROUND ? 1 : 0}, d_ * d_, umax(bl),
-         umax(br));
-    // 2. float32 preconditioning passes. Each pass runs a float32 one-sided Jacobi on a
-    //    float copy of the current W (V32 starts at I), makes V32 orthonormal to float64
-    //    rounding by a float64 Householder QR (V32 = Q R), and applies Q to W and V in
-    //    float64, so W V^T = Theta keeps holding exactly up to rounding. The first pass
-    //    works on Theta itself, whose float copy only resolves singular values above about
-    //    u32 ||Theta||; it stops at an absolute floor at that level. After it the columns
-    //    of W are graded (norms near the singular values), so a float copy keeps each
-    //    column to relative accuracy, and the later passes (relative test only, floor at
-    //    float64 rounding) resolve the rest of the spectrum. The float64 polish then starts
-    //    from couplings near the float32 test and converges in a few sweeps.
-    int wb = ws(WS_T), wo = ws(WS_X);            // current W, spare m x n buffer
-    int vb = -1;                                 // current V (-1: identity)
-    int vf[2] = {ws(WS_V2), ws(WS_V3)};          // free n x n buffers
-    int vspare = ws(WS_V);
+         umax(br), umax(bm), GemmShape{Dim{1, bl}, Dim{1, br}, Dim{1, bm}, d_ * d_, 0});
+    // 2. float32 one-sided Jacobi passes. Each runs on a float copy of the current W with V32
+    //    starting at I; then W <- W V32 and V <- V V32 in float64, so W = Theta V keeps holding
+    //    to float64 rounding (V is orthonormal only to float32 accuracy until step 3). The
+    //    first pass works on Theta itself, whose float copy only resolves singular values
+    //    above about u32 ||Theta||, so it stops at an absolute floor at that level and after
+    //    a few sweeps: it only has to grade W. After it the columns of W are graded (norms
+    //    near the singular values), a float copy keeps each column to relative accuracy, and
+    //    the next pass (relative test, floor at float64 rounding) resolves the rest of the
+    //    spectrum to float32 accuracy.
+    int wb = ws(WS_T), wo = ws(WS_X);  // current W (starts as Theta), spare m x n buffer
+    int vb = -1;                       // current V (-1: identity)
+    std::vector<int> fr = {ws(WS_V), ws(WS_V2), ws(WS_V3), ws(WS_G), ws(WS_R)};  // free n x n buffers
+    auto take = [&]() { int b = fr.back(); fr.pop_back(); return b; };
     for (int p = 0; p < npass; ++p) {
       cast(wb, ws(WS_W32), m, n, 1, (long)m_ub * n_ub);
-      const int sweeps32 = (p == 0 && npass > 1) ? kF32FirstPassSweeps : kF32Sweeps;
-      HestArgs h32{tab_, ws(WS_W32), ws(WS_V32), m, n, npad_ub, sweeps32,
-                   counters_ + (size_t)(sw32 + p) * counter_stride_,
-                   16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)),
-                   p == 0 ? 64 * 5.96e-8 : 64 * 1.11e-16,
-                   fro2_ + (size_t)(sw32 + p) * Z_, 1, ST_JFLOPS32, ws(WS_NRM), -1};
-      if (opt_.f32_block > 0) {
-        const int fb = opt_.f32_block;
-        const int nblk_ub = (n_ub + fb - 1) / fb;
-        const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
-        BJacArgs bj{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, sweeps32,
-                    h32.counters, h32.tol, h32.delta, h32.fro2, ST_JFLOPS32};
-        void* fn = fb == 8 ? (void*)block_jacobi_kernel<8> : (void*)block_jacobi_kernel<16>;
-        timed(1, [&] { coop(fn, &bj, bjac_blocks_per_sm(fb), (long)Z_ * (nblk_pad_ub / 2)); });
-      } else {
-        timed(1, [&] { coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs); });
-      }
-      // V32 -> float64 (QR input, overwritten by the reflectors) -> Q
-      const int qin = vf[0], qout = (vb < 0) ? vspare : vf[1];
-      cast(ws(WS_V32), qin, n, n, 0, (long)n_ub * n_ub);
-      QRArgs qa{tab_, qin, ws(WS_TAU), ws(WS_R), qout, n, n, nscr, n_ub, n_ub};
-      coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8);
-      // W <- W Q (float64)
-      gemm(ThetaVFn{tab_, wb, qout, wo, m, n}, 1, m_ub, n_ub);
+      const int sweeps32 = (p == 0 && npass > 1) ? kF32FirstPassSweeps : (opt_.max_sweeps > 0 ? opt_.max_sweeps : kF32Sweeps);
+      jacobi32(p, sw32 + p, m, n, m_ub, n_ub, npad_ub, pairs, sweeps32);
+      const int v32 = take();
+      cast(ws(WS_V32), v32, n, n, 0, (long)n_ub * n_ub);
+      if (p > 0 && tc_) colexp(wb, m, n, n_ub);              // W is graded from pass 1 on
+      gemm(ThetaVFn{tab_, wb, v32, wo, m, n}, 1, m_ub, n_ub, n_ub, GemmShape{m, n, n, 1, 0},
+           p > 0 && tc_ ? ws(WS_TAU) : -1);  // W <- W V32
       std::swap(wb, wo);
       if (vb < 0) {
-        vb = qout;                               // V = I Q; vf[0], vf[1] stay free
+        vb = v32;                                              // V = I V32
       } else {
-        // V <- V Q into the consumed QR input; the old V and Q become free
-        gemm(ThetaVFn{tab_, vb, qout, qin, n, n}, 1, n_ub, n_ub);
-        vf[0] = vb;
-        vf[1] = qout;
-        vb = qin;
+        const int vn = take();
+        gemm(ThetaVFn{tab_, vb, v32, vn, n, n}, 1, n_ub, n_ub, n_ub, GemmShape{n, n, n, 1, 0});  // V <- V V32
+        fr.push_back(vb);
+        fr.push_back(v32);
+        vb = vn;
       }
     }
-    // 3. float64 polish of all column pairs: the column norms become the singular values
-    //    to float64 accuracy, so the rank rule and the discarded weight of Eq. eps are
-    //    decided in float64.
+    if (vb < 0) {  // no float32 pass: start from V = I
+      vb = take();
+      cast(-1, vb, n, n, 2, (long)n_ub * n_ub);
+    }
+    // 3. float64 Newton steps (ttm_newton.cuh): couplings of W and the orthogonality defect
+    //    of V fall quadratically from float32 level to float64 rounding. The provisional
+    //    cut (Eq. eps + cap on the current column norms) tells which pairs can matter.
+    order_and_truncate(wb, m, n, nprov, 0, -1, n_ub, cap, kind == SK_ROUND ? bm : -1, ST_TRACE);
+    pcopy(wb, ws(WS_W0), m, n, -1, 0, (long)m_ub * n_ub);  // the state the fallback restarts from
+    pcopy(vb, ws(WS_V0), n, n, -1, 0, (long)n_ub * n_ub);
+    const int nsteps = newton_steps();
+    for (int s = 0; s < nsteps; ++s) {
+      const int g = take(), mm = take(), xb = take();
+      gemm(GramFn{tab_, wb, g, m, n}, 1, n_ub, n_ub, m_ub, GemmShape{n, n, m, 1, 1});
+      gemm(GramFn{tab_, vb, mm, n, n}, 1, n_ub, n_ub, n_ub, GemmShape{n, n, n, 1, 1});
+      newton_x(g, mm, xb, n, n_ub, nprov, s == 0 ? 1 : 0, 0, s + 1 == nsteps, -1);
+      if (tc_) colexp(wb, m, n, n_ub);
+      gemm(ThetaVFn{tab_, wb, xb, wo, m, n}, 1, m_ub, n_ub, n_ub, GemmShape{m, n, n, 1, 0},
+           tc_ ? ws(WS_TAU) : -1);  // W <- W X
+      std::swap(wb, wo);
+      gemm(ThetaVFn{tab_, vb, xb, mm, n, n}, 1, n_ub, n_ub, n_ub, GemmShape{n, n, n, 1, 0});  // V <- V X
+      fr.push_back(vb);
+      fr.push_back(g);
+      fr.push_back(xb);
+      vb = mm;
+    }
+    launch_small(newton_check_kernel, cdiv(Z_, 128), 128);
+    // 3b. fallback for the products whose Newton residual stayed above float64 level (every
+    //     launch below is empty for the others): restart from the state after the float32
+    //     passes, make V orthonormal by two polar steps, and run the float64 one-sided Jacobi
+    //     to convergence; then the result replaces the Newton one.
     {
-      const int polish_sweeps =
-          opt_.prec == TTM_PREC_MIXED_F32 ? (opt_.max_sweeps > 0 ? opt_.max_sweeps : 3) : max_sweeps();
-      int bcls = -1;
-      if (kd) {
-        // provisional order and rank from the preconditioned columns, then the membership
-        // of every column (cls in the tau workspace, free during the polish)
-        order_and_truncate(wb, m, n, nprov, 0, -1, n_ub, cap, nepsr);
-        ClassArgs ca{tab_, ws(WS_PERM), ws(WS_TAU), n, nprov, nepsr, (int)cap, opt_.eps};
-        classify_kernel<<<dim3(cdiv(n_ub, 256), Z_), 256, 0, hs_.stream>>>(ca);
-        TTM_CUDA(cudaGetLastError());
-        ++launches_;
-        bcls = ws(WS_TAU);
+      int fw = ws(WS_W0), fv = ws(WS_V0), fw2 = ws(WS_W0B);
+      for (int s = 0; s < 2; ++s) {
+        const int mm = take(), xb = take(), vn = take();
+        gemm(PredFn<GramFn>{GramFn{tab_, fv, mm, n, n}, IS_FALLBACK, 1, tab_}, 1, n_ub, n_ub, n_ub,
+             GemmShape{n, n, n, 1, 1});
+        newton_x(mm, mm, xb, n, n_ub, nprov, 0, 1, false, IS_FALLBACK);
+        if (tc_) colexp(fw, m, n, n_ub);
+        gemm(PredFn<ThetaVFn>{ThetaVFn{tab_, fw, xb, fw2, m, n}, IS_FALLBACK, 1, tab_}, 1, m_ub, n_ub, n_ub,
+             GemmShape{m, n, n, 1, 0}, tc_ ? ws(WS_TAU) : -1);
+        gemm(PredFn<ThetaVFn>{ThetaVFn{tab_, fv, xb, vn, n, n}, IS_FALLBACK, 1, tab_}, 1, n_ub, n_ub, n_ub,
+             GemmShape{n, n, n, 1, 0});
+        std::swap(fw, fw2);
+        fr.push_back(mm);
+        fr.push_back(xb);
+        if (fv != ws(WS_V0)) fr.push_back(fv);
+        fv = vn;
       }
-      HestArgs h64{tab_, wb, vb, m, n, npad_ub, polish_sweeps,
-                   counters_ + (size_t)sw64 * counter_stride_,
-                   1e-10, 64 * 1.11e-16,
-                   fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), bcls};
-      timed(0, [&] { coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs); });
+      HestArgs h64{tab_, fw, fv, m, n, npad_ub, kPolishSweeps, counters_ + (size_t)sw64 * counter_stride_, 1e-10,
+                   64 * 1.11e-16, fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), 1, IS_FALLBACK};
+      timed(1, [&] { coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs); });
+      pcopy(fw, wb, m, n, IS_FALLBACK, 1, (long)m_ub * n_ub);
+      pcopy(fv, vb, n, n, IS_FALLBACK, 1, (long)n_ub * n_ub);
+      if (fv != ws(WS_V0)) fr.push_back(fv);
     }
     // 4. final order by column norm, Eq. eps + cap, new carriages
-    order_and_truncate(wb, m, n, nbnd, 1, wslot, n_ub, cap);
+    order_and_truncate(wb, m, n, nbnd, 1, wslot, n_ub, cap, kind == SK_ROUND ? bm : -1);
     {
       ++launches_;
       GatherArgs ga{tab_, wb, vb, ws(WS_PERM), y, x, bl, br, nbnd, d_};
@@ -197,9 +209,33 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
   return nbnd;
 }
 
+// One float32 one-sided Jacobi pass on the W32 workspace (V32 starts at I): the scalar kernel
+// (one grid barrier per round of column pairs) or the block kernel (one per round of block
+// pairs). Pass 0 stops at an absolute floor at float32 rounding of ||W||, later passes at
+// float64 rounding.
+void Engine::jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int npad_ub, long pairs,
+                      int sweeps) {
+  HestArgs h32{tab_, ws(WS_W32), ws(WS_V32), m, n, npad_ub, sweeps,
+               counters_ + (size_t)slot * counter_stride_,
+               16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)),
+               pass == 0 ? 64 * 5.96e-8 : 64 * 1.11e-16,
+               fro2_ + (size_t)slot * Z_, 1, ST_JFLOPS32, ws(WS_NRM), pass > 0 ? 1 : 0, -1};
+  if (opt_.f32_block > 0) {
+    const int fb = opt_.f32_block;
+    const int nblk_ub = (n_ub + fb - 1) / fb;
+    const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
+    BJacArgs bj{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, sweeps,
+                h32.counters, h32.tol, h32.delta, h32.fro2, ST_JFLOPS32, h32.count_nonconv};
+    void* fn = fb == 8 ? (void*)block_jacobi_kernel<8> : (void*)block_jacobi_kernel<16>;
+    timed(1, [&] { coop(fn, &bj, bjac_blocks_per_sm(fb), (long)Z_ * (nblk_pad_ub / 2)); });
+  } else {
+    timed(1, [&] { coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs); });
+  }
+}
+
 // Column norms of W (workspace X), descending order, and the rank rule of Eq. eps.
 void Engine::order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, int wslot, int n_ub,
-                                long cap, int ieps) {
+                                long cap, int ikeep, int tslot) {
   launches_ += 3;
   NormArgs na{tab_, wbuf, ws(WS_NRM), m, n};
   dim3 g(cdiv(n_ub, 8), Z_);
@@ -209,7 +245,7 @@ void Engine::order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, i
   dim3 g2(cdiv(n_ub, 256), Z_);
   rank_kernel<<<g2, 256, 0, hs_.stream>>>(ra);
   TTM_CUDA(cudaGetLastError());
-  TruncArgs ta{tab_, ws(WS_SORT), m, n, ibond, opt_.eps, (int)cap, wslot, record, ieps};
+  TruncArgs ta{tab_, ws(WS_SORT), m, n, ibond, opt_.eps, (int)cap, wslot, record, ikeep, tslot};
   truncate_kernel<<<Z_, 1024, 0, hs_.stream>>>(ta);
   TTM_CUDA(cudaGetLastError());
 }
@@ -217,7 +253,8 @@ void Engine::order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, i
 void Engine::contract(int kb, int mb, int out, int il, int ia, int ir) {
   log_.push_back({SK_CONTRACT, il, ia, ir, 0});
   note_carriage(il, ir);
-  gemm(ContractFn{tab_, kb, mb, out, il, ia, ir, d_}, d_, umax(il), umax(ir));
+  gemm(ContractFn{tab_, kb, mb, out, il, ia, ir, d_}, d_, umax(il), umax(ir), umax(ia),
+       GemmShape{Dim{1, il}, Dim{1, ir}, Dim{1, ia}, d_, 0});
 }
 
 void Engine::run() {
@@ -311,6 +348,22 @@ void Engine::run() {
   // V^T to the right) truncate Omega's bonds 1, 2, ... with the rest of the train
   // orthonormal; then the mirror is undone. The centre ends on Pi_N.
   if (rounding()) {
+    // the rounding truncates only products with an output bond above chi_out (reading A4);
+    // the others go through the same sweep as exact refactorisations
+    if (launch_) {
+      std::vector<int> ids;
+      for (int j = 1; j < L; ++j) ids.push_back(piR[j]);
+      for (size_t c0 = 0; c0 < ids.size(); c0 += 32) {
+        RoundGateArgs ra{};
+        ra.t = tab_;
+        ra.n = (int)std::min<size_t>(32, ids.size() - c0);
+        for (int q = 0; q < ra.n; ++q) ra.ids[q] = ids[c0 + q];
+        ra.cap = (int)opt_.chi_out;
+        round_gate_kernel<<<Z_, 32, 0, hs_.stream>>>(ra);
+        TTM_CUDA(cudaGetLastError());
+        ++launches_;
+      }
+    }
     std::vector<int> mb(L + 1), mL(L + 1), mR(L + 1);
     for (int j = 1; j <= L; ++j) {
       const int src = pi[j], dst = get_buf();
@@ -355,7 +408,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   hbuf_.assign((size_t)Z_ * nb_, nullptr);
   const long ws_elems[] = {t_elems_,   v_elems_, vec_elems_, vec_elems_, vec_elems_,
                            vec_elems_, r_elems_, q_elems_,   t_elems_ / 2 + 1, v_elems_ / 2 + 1,
-                           x_elems_,   v_elems_, v_elems_};
+                           x_elems_,   v_elems_, v_elems_, v_elems_, t_elems_, v_elems_, t_elems_};
   static_assert(sizeof(ws_elems) / sizeof(ws_elems[0]) == WS_COUNT, "one size per workspace");
   for (int z = 0; z < Z_; ++z) {
     for (int bi = 0; bi < nchain_; ++bi) {
@@ -384,6 +437,8 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   off = align256(off + (size_t)n_jac * counter_stride_ * sizeof(int));
   fro2_ = (double*)(base + off);
   off = align256(off + (size_t)n_jac * Z_ * sizeof(double));
+  d_tc_ = (unsigned char*)(base + off);
+  off = align256(off + (size_t)tc_bytes_);
 
   std::vector<int> hb((size_t)Z_ * nbd, 0);
   for (int id = 0; id < nbd; ++id)
@@ -422,16 +477,20 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   TTM_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   if (hs_.ev0 && hs_.ev1) TTM_CUDA(cudaEventElapsedTime(&ms, hs_.ev0, hs_.ev1));
-  double jac_ms = 0.0, jac32_ms = 0.0;
+  double kind_ms[3] = {0.0, 0.0, 0.0};  // GEMMs, float32 Jacobi, Householder QR
   for (int q = 0; q + 1 < prof_used_; q += 2) {
     float x = 0.f;
     TTM_CUDA(cudaEventElapsedTime(&x, hs_.prof_events[q], hs_.prof_events[q + 1]));
-    if (prof_kind_[q / 2] == 1)
-      jac32_ms += x;
-    else
-      jac_ms += x;
+    kind_ms[prof_kind_[q / 2]] += x;
   }
 
+  for (int z = 0; z < Z_; ++z) {
+    const int st_z = istat[(size_t)z * nis + IS_STATUS];
+    if (st_z == (int)TTM_ERR_TIMEOUT)
+      throw Error(TTM_ERR_TIMEOUT, "a tensor-core pipeline wait hit its time limit");
+    if (st_z == (int)TTM_ERR_NONFINITE)
+      throw Error(TTM_ERR_NONFINITE, "product " + std::to_string(z) + ": a Swap met a non-finite value");
+  }
   for (int z = 0; z < Z_; ++z) {
     auto bv = [&](int id) { return (long)bonds[(size_t)z * nbd + id]; };
     ttm_tt& o = outs[z];
@@ -484,13 +543,26 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     r.err_bound = stat[(size_t)z * ns + ST_WSQRT];
     r.seconds = ms * 1e-3;
     r.peak_workspace_bytes = (int64_t)bytes_needed();
-    if (istat[(size_t)z * nis + IS_NONCONV] > 0) r.status = TTM_OK;  // result valid; optimality not guaranteed
+    r.newton_residual = stat[(size_t)z * ns + ST_NEWTON_RES];
+    r.n_nonconverged = istat[(size_t)z * nis + IS_NONCONV];
+    r.n_fallback = istat[(size_t)z * nis + IS_NEWTON_BAD];
+    r.n_frozen_pairs = istat[(size_t)z * nis + IS_NFROZEN];
+    if (r.n_nonconverged > 0) r.status = TTM_WARN_NOT_CONVERGED;  // result formed; optimality not guaranteed
     r.n_kernel_launches = launches_;
     r.jacobi_launches = jac_launch_;
-    r.jacobi_ms = jac_ms;
-    r.jacobi_flops = stat[(size_t)0 * ns + ST_JFLOPS];  // float64 polish, launch-wide (all products)
-    r.jacobi32_ms = jac32_ms;
+    r.gemm_ms = kind_ms[0];
+    r.jacobi32_ms = kind_ms[1];
+    r.qr_ms = kind_ms[2];
     r.jacobi32_flops = stat[(size_t)0 * ns + ST_JFLOPS32];
+    r.gemm_launches = (int64_t)gemm_log_.size();
+    double gf = 0.0;
+    for (const GemmShape& gs : gemm_log_)
+      for (int zz = 0; zz < Z_; ++zz) {  // launch-wide, like the other kernel figures
+        auto dv = [&](const Dim& dd) { return dd.id < 0 ? (double)dd.mul : (double)dd.mul * bonds[(size_t)zz * nbd + dd.id]; };
+        const double M = dv(gs.M), N = dv(gs.N), K = dv(gs.K);
+        gf += gs.nbatch * (gs.sym ? M * (N + 1) * K : 2.0 * M * N * K);
+      }
+    r.gemm_flops = gf;
     r.bond_trace = (int64_t*)user_trace;
     r.bond_trace_len = 0;
     if (user_trace) {
@@ -546,20 +618,19 @@ static ttm_status check_tt(const ttm_tt* t, const char* name, bool need_cores) {
 static ttm_status check_opts(const ttm_options& o) {
   if (!(o.eps >= 0.0 && o.eps < 1.0)) return set_err(TTM_ERR_INVALID_ARG, "eps must lie in [0, 1)");
   if (o.chi_max < 0 || o.chi_out < 0) return set_err(TTM_ERR_INVALID_ARG, "negative cap");
-  if (o.prec != TTM_PREC_FP64 && o.prec != TTM_PREC_TF32X3 && o.prec != TTM_PREC_BF16X3 &&
-      o.prec != TTM_PREC_MIXED_F32)
+  if (o.prec != TTM_PREC_FP64 && o.prec != TTM_PREC_BF16_SPLIT)
     return set_err(TTM_ERR_INVALID_ARG, "unknown precision mode");
-  if (o.prec == TTM_PREC_TF32X3 || o.prec == TTM_PREC_BF16X3)
-    return set_err(TTM_ERR_UNSUPPORTED, "tensor-core split precision modes are not built");
   if (o.use_graph != 0 || o.check_finite != 0)
     return set_err(TTM_ERR_UNSUPPORTED, "use_graph and check_finite are not built (must be 0)");
   if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)
     return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
   if (o.f32_block != 0 && o.f32_block != 8 && o.f32_block != 16)
     return set_err(TTM_ERR_INVALID_ARG, "f32_block must be 0, 8 or 16");
-  if (o.polish_kept_dropped != 0 && o.polish_kept_dropped != 1)
-    return set_err(TTM_ERR_INVALID_ARG, "polish_kept_dropped must be 0 or 1");
-  if (o.reserved1 != 0) return set_err(TTM_ERR_INVALID_ARG, "reserved option field must be 0");
+  if (o.newton_steps < 0 || o.newton_steps > kMaxNewtonSteps)
+    return set_err(TTM_ERR_INVALID_ARG, "newton_steps must lie in [0, 8]");
+  if (o.max_sweeps < 0 || o.max_sweeps > 1000) return set_err(TTM_ERR_INVALID_ARG, "max_sweeps must lie in [0, 1000]");
+  if (o.split_digits != 0 && (o.split_digits < 2 || o.split_digits > kOzMaxS))
+    return set_err(TTM_ERR_INVALID_ARG, "split_digits must be 0 or lie in [2, 8]");
   return TTM_OK;
 }
 
@@ -599,6 +670,11 @@ static ttm_status multiply_impl(ttm_handle* h, int32_t n, const ttm_tt* A, const
     e.execute(h->s.arena.ptr, h->s.opt, &reps, out);
     if (rep)
       for (int i = 0; i < n; ++i) rep[i] = reps[i];
+    for (int i = 0; i < n; ++i)
+      if (reps[i].status == TTM_WARN_NOT_CONVERGED)
+        return set_err(TTM_WARN_NOT_CONVERGED, "product " + std::to_string(i) + ": " +
+                                                   std::to_string(reps[i].n_nonconverged) +
+                                                   " Swap SVD(s) did not converge");
   } catch (const Error& err) {
     return set_err(err.status, err.what());
   } catch (const std::exception& ex) {
@@ -627,8 +703,8 @@ ttm_status ttm_create(ttm_handle** h, int device, void* cuda_stream, const ttm_o
     H->s.stream = (cudaStream_t)cuda_stream;
     H->s.opt = o;
     TTM_CUDA(cudaDeviceGetAttribute(&H->s.num_sms, cudaDevAttrMultiProcessorCount, device));
-    TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&H->s.coop_hest, hestenes_kernel<double>, 256, 0));
     TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&H->s.coop_hest32, hestenes_kernel<float>, 256, 0));
+    TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&H->s.coop_hest, hestenes_kernel<double>, 256, 0));
     TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&H->s.coop_qr, householder_kernel, 256, 0));
     int coop = 0;
     TTM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
@@ -773,7 +849,7 @@ namespace {
 struct NoAllocDevice {
   bool ready = false;
   void* scratch = nullptr;
-  int num_sms = 0, coop_hest = 0, coop_hest32 = 0, coop_qr = 0;
+  int num_sms = 0, coop_hest32 = 0, coop_hest = 0, coop_qr = 0;
 };
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[64];
@@ -806,8 +882,8 @@ ttm_status ttm_multiply_noalloc(const ttm_tt* A, const ttm_tt* B, ttm_tt* out, c
         void* p = nullptr;
         TTM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         TTM_CUDA(cudaDeviceGetAttribute(&nd.num_sms, cudaDevAttrMultiProcessorCount, dev));
-        TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd.coop_hest, hestenes_kernel<double>, 256, 0));
         TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd.coop_hest32, hestenes_kernel<float>, 256, 0));
+        TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd.coop_hest, hestenes_kernel<double>, 256, 0));
         TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd.coop_qr, householder_kernel, 256, 0));
         nd.scratch = p;
         nd.ready = true;
@@ -819,8 +895,8 @@ ttm_status ttm_multiply_noalloc(const ttm_tt* A, const ttm_tt* B, ttm_tt* out, c
     hs.stream = (cudaStream_t)cuda_stream;
     hs.opt = o;
     hs.num_sms = info.num_sms;
-    hs.coop_hest = info.coop_hest;
     hs.coop_hest32 = info.coop_hest32;
+    hs.coop_hest = info.coop_hest;
     hs.coop_qr = info.coop_qr;
     Engine e(hs, 1, A, B);
     e.plan();
@@ -832,10 +908,75 @@ ttm_status ttm_multiply_noalloc(const ttm_tt* A, const ttm_tt* B, ttm_tt* out, c
     std::vector<ttm_report> reps(1);
     std::memset(&reps[0], 0, sizeof(ttm_report));
     e.execute(info.scratch, o, &reps, out);
+    if (reps[0].status == TTM_WARN_NOT_CONVERGED)
+      return set_err(TTM_WARN_NOT_CONVERGED, std::to_string(reps[0].n_nonconverged) +
+                                                 " Swap SVD(s) did not converge");
   } catch (const Error& err) {
     return set_err(err.status, err.what());
   } catch (const std::exception& ex) {
     return set_err(TTM_ERR_INVALID_ARG, ex.what());
+  }
+  return TTM_OK;
+}
+
+// ---------------------------------------------------------------- plain GEMM
+
+namespace {
+// C = A B with column-major device matrices (one problem per launch).
+struct RawGemmFn {
+  Tables t;
+  int M, N, K;
+  const double* A;
+  long lda;
+  const double* B;
+  long ldb;
+  double* C;
+  long ldc;
+  __device__ GemmDesc operator()(int, int) const {
+    GemmDesc g;
+    g.M = M; g.N = N; g.K = K;
+    g.A = MatRef{A, 1, lda};
+    g.B = MatRef{B, 1, ldb};
+    g.C = OutRef{C, 1, ldc};
+    g.alpha = 1.0; g.beta = 0.0; g.upper = 0;
+    return g;
+  }
+};
+}  // namespace
+
+ttm_status ttm_gemm(ttm_handle* h, ttm_precision prec, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double* C, int64_t ldc) {
+  if (!h || !A || !B || !C) return set_err(TTM_ERR_INVALID_ARG, "null argument");
+  if (M < 1 || N < 1 || K < 1 || M > (1 << 20) || N > (1 << 20) || K > (1 << 20))
+    return set_err(TTM_ERR_SHAPE, "M, N, K must lie in [1, 2^20]");
+  if (lda < M || ldb < K || ldc < M) return set_err(TTM_ERR_SHAPE, "leading dimension below the row count");
+  if (prec != TTM_PREC_FP64 && prec != TTM_PREC_BF16_SPLIT) return set_err(TTM_ERR_INVALID_ARG, "unknown precision mode");
+  try {
+    TTM_CUDA(cudaSetDevice(h->s.device));
+    Tables t{};
+    RawGemmFn f{t, (int)M, (int)N, (int)K, A, (long)lda, B, (long)ldb, C, (long)ldc};
+    cudaStream_t st = h->s.stream;
+    if (prec == TTM_PREC_FP64) {
+      dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT), 1);
+      dgemm_kernel<RawGemmFn><<<grid, 256, 0, st>>>(f, 1);
+      TTM_CUDA(cudaGetLastError());
+    } else {
+      const int S = h->s.opt.split_digits > 0 ? h->s.opt.split_digits : kOzMaxS;
+      const size_t need = tc_ws_bytes(1, (int)M, (int)N, (int)K, S) + 256;
+      h->s.env_arena.ensure(need);
+      unsigned char* ws = (unsigned char*)h->s.env_arena.ptr;
+      int* err = (int*)(ws + need - 256);
+      TTM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+      launch_tc_gemm(st, f, 1, 1, (int)M, (int)N, (int)K, -1, S, ws, err);
+      TTM_CUDA(cudaGetLastError());
+      int herr = 0;
+      TTM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TTM_CUDA(cudaStreamSynchronize(st));
+      if (herr != 0) throw Error(TTM_ERR_TIMEOUT, "a tensor-core pipeline wait hit its time limit");
+    }
+    TTM_CUDA(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
+  } catch (const Error& err) {
+    return set_err(err.status, err.what());
   }
   return TTM_OK;
 }

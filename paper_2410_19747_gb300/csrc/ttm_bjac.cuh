@@ -34,6 +34,7 @@ struct BJacArgs {
   double delta;      // ... and |G_pq| > delta * sqrt(max(G_pp, G_qq)) * ||W||_F
   double* fro2;      // [nz] ||W||_F^2, zeroed before launch
   int flop_slot;     // stat slot that accumulates the executed flops
+  int count_nonconv; // 1: a product that hits max_sweeps counts in IS_NONCONV
 };
 
 __device__ __forceinline__ int bj_ldcg(const int* p) { return __ldcg(p); }
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(BJacArgs a) {
       }
       int* is = a.t.istat + z * a.t.nis;
       if (used > is[IS_SWEEPS_MAX]) is[IS_SWEEPS_MAX] = used;
-      if (!conv && a.n.eval(a.t, z) > 1) is[IS_NONCONV] += 1;
+      if (a.count_nonconv && !conv && a.n.eval(a.t, z) > 1) is[IS_NONCONV] += 1;
     }
   }
 }

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ttm.h"
+
 namespace ttm {
 
 struct Tables {
@@ -34,9 +36,14 @@ __device__ __forceinline__ double* bufp(const Tables& t, int z, int id) {
 }
 
 // istat slots
-enum { IS_STATUS = 0, IS_MAX_BOND = 1, IS_SWEEPS_MAX = 2, IS_NONCONV = 3, IS_NFIXED = 4 };
-// stat slots (the per-truncation weights follow from ST_W0)
-enum { ST_WSUM = 0, ST_WSQRT = 1, ST_JFLOPS = 2, ST_JFLOPS32 = 3, ST_NFIXED = 4 };
+enum { IS_STATUS = 0, IS_MAX_BOND = 1, IS_SWEEPS_MAX = 2, IS_NONCONV = 3, IS_NFROZEN = 4, IS_NEWTON_BAD = 5,
+       IS_ROUND = 6, IS_CAST_EXP = 7, IS_FALLBACK = 8, IS_NFIXED = 9 };
+// stat slots (the per-truncation weights follow from ST_NFIXED)
+enum { ST_WSUM = 0, ST_WSQRT = 1, ST_NEWTON_RES = 2, ST_JFLOPS32 = 3, ST_NEWTON_CUR = 4, ST_TRACE = 5,
+       ST_JFLOPS = 6, ST_NFIXED = 7 };
+
+// Residual of the last Newton step of an SVD above which it counts as not converged.
+constexpr double kNewtonConverged = 1e-8;
 
 // A dimension written as mul * bond[id] (id < 0 means the constant mul).
 struct Dim {

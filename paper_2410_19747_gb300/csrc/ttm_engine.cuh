@@ -19,6 +19,8 @@
 #include "ttm_qr.cuh"
 #include "ttm_svd.cuh"
 #include "ttm_bjac.cuh"
+#include "ttm_newton.cuh"
+#include "ttm_tc.cuh"
 
 namespace ttm {
 
@@ -31,7 +33,8 @@ struct StepLog {
 class Engine {
  public:
   Engine(HandleState& hs, int Z, const ttm_tt* A, const ttm_tt* B)
-      : hs_(hs), Z_(Z), A_(A), B_(B), L_(A[0].L), d_(A[0].d), opt_(hs.opt) {}
+      : hs_(hs), Z_(Z), A_(A), B_(B), L_(A[0].L), d_(A[0].d), opt_(hs.opt),
+        tc_(hs.opt.prec == TTM_PREC_BF16_SPLIT) {}
 
   // ------------------------------------------------------------------ planning
   void plan() {
@@ -43,7 +46,7 @@ class Engine {
     nb_ = nchain_ + WS_COUNT;
   }
 
-  size_t bytes_needed() const { return per_product_bytes() * Z_ + table_bytes(); }
+  size_t bytes_needed() const { return per_product_bytes() * Z_ + table_bytes() + (size_t)tc_bytes_ + 256; }
 
   // ------------------------------------------------------------------ execution
   void execute(void* arena, const ttm_options& opt, std::vector<ttm_report>* reps, ttm_tt* outs);
@@ -55,7 +58,7 @@ class Engine {
  private:
   enum {
     WS_T = 0, WS_V, WS_NRM, WS_SORT, WS_PERM, WS_TAU, WS_R, WS_Q, WS_W32, WS_V32, WS_X, WS_V2, WS_V3,
-    WS_COUNT
+    WS_G, WS_W0, WS_V0, WS_W0B, WS_COUNT
   };
 
   HandleState& hs_;
@@ -65,6 +68,9 @@ class Engine {
   int L_, d_;
   ttm_options opt_{};
   bool launch_ = false;
+  bool tc_ = false;          // GEMM-shaped work on the tensor cores (TTM_PREC_BF16_SPLIT)
+  long tc_bytes_ = 0;        // digit workspace of the largest tensor-core GEMM (planned)
+  unsigned char* d_tc_ = nullptr;
   // ids
   std::vector<std::vector<int>> ub_;  // ub_[id][z]
   std::vector<std::vector<int>> exact_;  // exact host values for input bonds, else empty
@@ -91,6 +97,7 @@ class Engine {
   std::vector<double*> hbuf_;  // host copy of the buffer table
 
   void reset_ids() {
+    gemm_log_.clear();
     ub_.clear();
     exact_.clear();
     free_bufs_.clear();
@@ -131,7 +138,7 @@ class Engine {
   int ws(int w) const { return nchain_ + w; }
 
   size_t per_product_bytes() const {
-    long e = (long)nchain_ * carriage_elems_ + t_elems_ + 3 * v_elems_ + 3 * vec_elems_ + vec_elems_ +
+    long e = (long)nchain_ * carriage_elems_ + 3 * t_elems_ + 5 * v_elems_ + 3 * vec_elems_ + vec_elems_ +
              r_elems_ + q_elems_ + (t_elems_ / 2 + 1) + (v_elems_ / 2 + 1) + x_elems_;
     // every buffer aligned to 256 bytes
     return (size_t)e * 8 + (size_t)(nb_ + 1) * 256;
@@ -146,21 +153,76 @@ class Engine {
     b += (size_t)std::max(1, jac_launch_) * Z_ * sizeof(double) + 256;
     return b;
   }
-  int max_sweeps() const { return opt_.max_sweeps > 0 ? opt_.max_sweeps : kDefaultSweeps; }
-  // Sweep counters per product and Jacobi launch: room for the float64 limit and for the
-  // fixed limit of the float32 passes.
-  int counter_sweeps() const { return std::max(max_sweeps(), kF32Sweeps); }
+  // Sweep counters per product and Jacobi launch: room for the sweep limit of any pass.
+  int counter_sweeps() const {
+    return std::max(std::max(opt_.max_sweeps, kPolishSweeps), std::max(kF32Sweeps, kF32FirstPassSweeps));
+  }
   int f32_passes() const {
     return opt_.f32_passes > 0 ? std::min(opt_.f32_passes, kMaxF32Passes) : kDefaultF32Passes;
+  }
+  int split_digits() const { return opt_.split_digits > 0 ? opt_.split_digits : kOzMaxS; }
+  int newton_steps() const {
+    return opt_.newton_steps > 0 ? std::min(opt_.newton_steps, kMaxNewtonSteps) : kDefaultNewtonSteps;
   }
 
   // grid helpers
   static unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
+  // C = A B of every (product, batch index) the functor describes: on the float64 pipe, or
+  // (tc_) as the exactly sliced bf16 product on the tensor cores (ttm_tc.cuh). kscale_buf:
+  // per-K power-of-two exponents that keep a graded A relatively accurate (tensor cores only).
+  // shape: the realised M x N x K of every batch index (for the flop count of the report).
   template <class F>
-  void gemm(const F& f, int nbatch, int M_ub, int N_ub) {
+  void gemm(const F& f, int nbatch, int M_ub, int N_ub, int K_ub, GemmShape shape, int kscale_buf = -1) {
+    if (tc_) {
+      tc_bytes_ = std::max(tc_bytes_, (long)tc_ws_bytes((long)Z_ * nbatch, M_ub, N_ub, K_ub, split_digits()));
+    }
     if (!launch_) return;
-    dim3 grid(cdiv(N_ub, GT), cdiv(M_ub, GT), (unsigned)(Z_ * nbatch));
-    dgemm_kernel<F><<<grid, 256, 0, hs_.stream>>>(f, nbatch);
+    gemm_log_.push_back(shape);
+    timed(0, [&] {
+      if (tc_) {
+        launch_tc_gemm(hs_.stream, f, Z_, nbatch, M_ub, N_ub, K_ub, kscale_buf, split_digits(), d_tc_,
+                       d_istat_ + IS_STATUS);
+        TTM_CUDA(cudaGetLastError());
+        launches_ += 6;
+      } else {
+        dim3 grid(cdiv(N_ub, GT), cdiv(M_ub, GT), (unsigned)(Z_ * nbatch));
+        dgemm_kernel<F><<<grid, 256, 0, hs_.stream>>>(f, nbatch);
+        TTM_CUDA(cudaGetLastError());
+        ++launches_;
+      }
+    });
+  }
+  // Predicated copy of a float64 rows x cols buffer (islot < 0: every product).
+  void pcopy(int src, int dst, Dim rows, Dim cols, int islot, int want, long n_ub) {
+    if (!launch_) return;
+    PredCopyArgs pa{tab_, src, dst, rows, cols, islot, want};
+    pred_copy_kernel<<<dim3((unsigned)std::min<long>(1024, cdiv(n_ub, 256)), Z_), 256, 0, hs_.stream>>>(pa);
+    TTM_CUDA(cudaGetLastError());
+    ++launches_;
+  }
+  // X of a Newton step from G and M (ttm_newton.cuh).
+  void newton_x(int g, int mm, int xb, Dim n, int n_ub, int nprov, int graded_only, int eonly, bool last,
+                int islot_pred) {
+    if (!launch_) return;
+    NewtonArgs na{tab_, g, mm, xb, n, ws(WS_SORT), nprov, ST_TRACE, graded_only, eonly,
+                  last ? ST_NEWTON_CUR : -1, last ? IS_NFROZEN : -1, islot_pred};
+    dim3 blk(32, 8), grd(cdiv(n_ub, 32), cdiv(n_ub, 8), Z_);
+    newton_x_kernel<<<grd, blk, 0, hs_.stream>>>(na);
+    TTM_CUDA(cudaGetLastError());
+    ++launches_;
+  }
+  template <class K>
+  void launch_small(K kernel, unsigned grid, unsigned block) {
+    if (!launch_) return;
+    kernel<<<grid, block, 0, hs_.stream>>>(tab_);
+    TTM_CUDA(cudaGetLastError());
+    ++launches_;
+  }
+  // Per-column power-of-two exponents of W (the K scale of W X) into the tau workspace.
+  void colexp(int wbuf, Dim m, Dim n, int n_ub) {
+    if (!launch_) return;
+    ColExpArgs ca{tab_, wbuf, ws(WS_TAU), m, n};
+    colexp_kernel<<<dim3(cdiv(n_ub, 8), Z_), 256, 0, hs_.stream>>>(ca);
     TTM_CUDA(cudaGetLastError());
     ++launches_;
   }
@@ -176,6 +238,11 @@ class Engine {
     if (!launch_) return;
     CastArgs ca{tab_, src, dst, rows, cols, to_float};
     dim3 g((unsigned)std::min<long>(1024, cdiv(n_ub, 256)), Z_);
+    if (to_float == 1) {  // float copies are scaled to max |W| near 1
+      reset_cast_exp_kernel<<<cdiv(Z_, 256), 256, 0, hs_.stream>>>(tab_);
+      absmax_exp_kernel<<<g, 256, 0, hs_.stream>>>(ca);
+      launches_ += 2;
+    }
     cast_kernel<<<g, 256, 0, hs_.stream>>>(ca);
     TTM_CUDA(cudaGetLastError());
     ++launches_;
@@ -206,7 +273,8 @@ class Engine {
   }
   long launches_ = 0;
   int prof_used_ = 0;
-  std::vector<int> prof_kind_;  // per event pair: 0 float64 polish, 1 float32 pass
+  std::vector<int> prof_kind_;  // per event pair: 0 GEMM, 1 float32 Jacobi pass, 2 Householder QR
+  std::vector<GemmShape> gemm_log_;  // every GEMM of the launch walk (flop count of the report)
   cudaEvent_t prof_event() {
     if (prof_used_ >= (int)hs_.prof_events.size()) {
       cudaEvent_t e;
@@ -233,10 +301,20 @@ class Engine {
   void load_core(const ttm_tt* T, int k, int buf);
   void qr_move(int c, int& nx, int bl, int& br, int brr);
   int swap(int x, int y, int bl, int bm, int br, int kind = SK_SWAP);
+  void jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int npad_ub, long pairs, int sweeps);
   void order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, int wslot, int n_ub, long cap,
-                          int ieps = -1);
-  // Final rounding (a7): runs when chi_out caps the output below the Swap cap.
-  bool rounding() const { return opt_.chi_out > 0 && (opt_.chi_max == 0 || opt_.chi_out < opt_.chi_max); }
+                          int ikeep = -1, int tslot = -1);
+  // Final rounding (a7): planned when an output bond can exceed chi_out (the Swap cap is
+  // above it, or absent, or an input bond is); the device gate (round_gate_kernel) then
+  // truncates only the products whose output has a bond above chi_out.
+  bool rounding() const {
+    if (opt_.chi_out <= 0) return false;
+    if (opt_.chi_max == 0 || opt_.chi_out < opt_.chi_max) return true;
+    for (int z = 0; z < Z_; ++z)
+      for (int i = 0; i <= L_; ++i)
+        if (A_[z].bonds[i] > opt_.chi_out || B_[z].bonds[i] > opt_.chi_out) return true;
+    return false;
+  }
   void contract(int kb, int mb, int out, int il, int ia, int ir);
   void run();
 };

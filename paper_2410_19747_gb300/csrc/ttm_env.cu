@@ -48,7 +48,7 @@ struct GenFn {
     g.A = MatRef{A.p + b1 * A.s1 + b2 * A.s2, A.rs, A.cs};
     g.B = MatRef{B.p + b1 * B.s1 + b2 * B.s2, B.rs, B.cs};
     g.C = OutRef{C.p + b1 * C.s1 + b2 * C.s2, C.rs, C.cs};
-    g.alpha = alpha; g.beta = beta;
+    g.alpha = alpha; g.beta = beta; g.upper = 0;
     return g;
   }
 };

@@ -28,9 +28,17 @@ struct GemmDesc {
   MatRef A, B;
   OutRef C;
   double alpha, beta;
+  int upper;  // 1: only the output tiles that meet the upper triangle (symmetric results)
 };
 
 constexpr int GT = 64, GK = 16;
+
+// Realised shape of a launch's GEMMs (per product and batch index), for the flop count.
+struct GemmShape {
+  Dim M, N, K;
+  int nbatch;
+  int sym;  // 1: symmetric result, only the upper triangle is counted
+};
 
 template <class F>
 __global__ void __launch_bounds__(256) dgemm_kernel(F f, int nbatch) {
@@ -38,6 +46,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(F f, int nbatch) {
   const GemmDesc g = f(z, bi);
   const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
   if (g.M <= 0 || g.N <= 0 || m0 >= g.M || n0 >= g.N) return;
+  if (g.upper && m0 > n0) return;
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   const int tid = threadIdx.x;
@@ -126,7 +135,7 @@ struct ThetaFn {
     g.A = MatRef{X + (long)s * Dm, (long)d * Dm, 1};
     g.B = MatRef{Y + (long)tt * Dr, (long)d * Dr, 1};
     g.C = OutRef{T + row_leg + (long)col_leg * Dr * mrows, d, mrows};
-    g.alpha = 1.0; g.beta = 0.0;
+    g.alpha = 1.0; g.beta = 0.0; g.upper = 0;
     return g;
   }
 };
@@ -145,7 +154,7 @@ struct ContractFn {
     g.A = MatRef{bufp(t, z, bk) + (long)e * Da, (long)d * Da, 1};
     g.B = MatRef{bufp(t, z, bm) + (long)e * Dr, (long)d * Dr, 1};
     g.C = OutRef{bufp(t, z, bo) + (long)e * Dr, (long)d * Dr, 1};
-    g.alpha = 1.0; g.beta = 0.0;
+    g.alpha = 1.0; g.beta = 0.0; g.upper = 0;
     return g;
   }
 };
@@ -164,7 +173,7 @@ struct RMergeFn {
     g.A = MatRef{bufp(t, z, br), n, 1};
     g.B = MatRef{bufp(t, z, bn), (long)d * Drr, 1};
     g.C = OutRef{bufp(t, z, bo), (long)d * Drr, 1};
-    g.alpha = 1.0; g.beta = 0.0;
+    g.alpha = 1.0; g.beta = 0.0; g.upper = 0;
     return g;
   }
 };
@@ -181,7 +190,26 @@ struct ThetaVFn {
     g.A = MatRef{bufp(t, z, bth), 1, M};
     g.B = MatRef{bufp(t, z, bv), 1, N};
     g.C = OutRef{bufp(t, z, bw), 1, M};
-    g.alpha = 1.0; g.beta = 0.0;
+    g.alpha = 1.0; g.beta = 0.0; g.upper = 0;
+    return g;
+  }
+};
+
+// Gram matrix G = W^T W of a column-major m x n matrix (n x n column-major; the tiles of
+// the upper triangle only: G is symmetric and its readers take G[min(i,j) + max(i,j) n]).
+struct GramFn {
+  Tables t;
+  int bw, bg;
+  Dim m, n;
+  __device__ GemmDesc operator()(int z, int) const {
+    const int M = m.eval(t, z), N = n.eval(t, z);
+    const double* W = bufp(t, z, bw);
+    GemmDesc g;
+    g.M = N; g.N = N; g.K = M;
+    g.A = MatRef{W, M, 1};
+    g.B = MatRef{W, 1, M};
+    g.C = OutRef{bufp(t, z, bg), 1, N};
+    g.alpha = 1.0; g.beta = 0.0; g.upper = 1;
     return g;
   }
 };
@@ -202,7 +230,7 @@ struct LMergeFn {
     g.A = MatRef{bufp(t, z, bp), c, 1};
     g.B = MatRef{bufp(t, z, bw), 1, ld};
     g.C = OutRef{bufp(t, z, bo), k, 1};
-    g.alpha = 1.0; g.beta = 0.0;
+    g.alpha = 1.0; g.beta = 0.0; g.upper = 0;
     return g;
   }
 };

@@ -26,11 +26,13 @@ struct Error : std::runtime_error {
                                            " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
   } while (0)
 
-constexpr int kMaxBond = 8192;      // largest bond the planner accepts
-constexpr int kDefaultSweeps = 40;  // one-sided Jacobi sweep limit
-constexpr int kDefaultF32Passes = 3;  // float32 preconditioning passes of every Swap SVD
+constexpr int kMaxBond = 8192;         // largest bond the planner accepts
+constexpr int kDefaultF32Passes = 2;   // float32 Jacobi passes of every Swap SVD
 constexpr int kMaxF32Passes = 8;
-constexpr int kF32Sweeps = 30;  // sweep limit of the later float32 passes
+constexpr int kF32Sweeps = 30;         // sweep limit of the later float32 passes
+constexpr int kDefaultNewtonSteps = 3; // float64 Newton steps after the float32 passes
+constexpr int kMaxNewtonSteps = 8;
+constexpr int kPolishSweeps = 40;      // sweep limit of the float64 Jacobi of the fallback
 // Sweep limit of the first float32 pass: it only has to grade W (the next pass redoes the
 // whole Jacobi on the graded W), so its refining sweeps are dropped.
 constexpr int kF32FirstPassSweeps = 3;
@@ -61,7 +63,7 @@ struct HandleState {
   cudaStream_t stream = nullptr;
   ttm_options opt{};
   int num_sms = 0;
-  int coop_hest = 0, coop_hest32 = 0, coop_qr = 0;  // co-resident blocks per SM (cooperative kernels)
+  int coop_hest32 = 0, coop_hest = 0, coop_qr = 0;  // co-resident blocks per SM (cooperative kernels)
   DeviceArena arena;      // sweep buffers and workspaces
   DeviceArena env_arena;  // environments of ttm_inner / ttm_inner3 / ttm_backward
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

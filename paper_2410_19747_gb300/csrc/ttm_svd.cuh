@@ -36,11 +36,8 @@ struct HestArgs {
   int init_v;        // 1: start from V = I; 0: V holds a starting rotation
   int flop_slot;     // stat slot that accumulates the executed flops
   int bmark;         // workspace of n ints: last sweep in which each column was rotated
-  int bcls;          // -1, or n+1 ints: cls[j] = 1 for columns kept by the truncation,
-                     // 0 otherwise, and cls[n] = the polish mode of the product:
-                     // 0 none, 1 only pairs with one kept and one dropped column (the
-                     // rotations inside either set leave the truncated tensor W_K V_K^T
-                     // unchanged), 2 all pairs.
+  int count_nonconv; // 1: a product that hits max_sweeps counts in IS_NONCONV
+  int islot_pred;    // -1, or istat slot: only products whose slot is non-zero take part
 };
 
 template <typename T>
@@ -112,8 +109,15 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
   // different SMs, so a round with fewer items than warps still uses every SM.
   const long gwarp = (long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = nthreads >> 5;
   const int nz = a.t.nz;
+  auto active = [&](int z) { return a.islot_pred < 0 || a.t.istat[z * a.t.nis + a.islot_pred] != 0; };
+  {  // every CTA reads the same flags, so all leave together before the first barrier
+    bool any = false;
+    for (int z = 0; z < nz; ++z) any = any || active(z);
+    if (!any) return;
+  }
 
   for (int z = 0; z < nz; ++z) {
+    if (!active(z)) continue;
     const int n = a.n.eval(a.t, z), m = a.m.eval(a.t, z);
     T* V = reinterpret_cast<T*>(bufp(a.t, z, a.bv));
     const long tot = (long)n * n;
@@ -129,12 +133,6 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
   }
   grid.sync();
 
-  if (a.bcls >= 0) {  // nothing to polish in any product: leave before the rounds
-    bool any = false;
-    for (int z = 0; z < nz; ++z)
-      if (reinterpret_cast<const int*>(bufp(a.t, z, a.bcls))[a.n.eval(a.t, z)] != 0) any = true;
-    if (!any) return;
-  }
   constexpr int kChunk = ChunkOf<T>::value;
   const int half = a.npad_ub / 2;
   const long items = (long)nz * half;
@@ -144,6 +142,7 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
     for (int r = 0; r < a.npad_ub - 1; ++r) {
       for (long it = gwarp; it < items; it += nwarps) {
         const int z = (int)(it / half), i = (int)(it % half);
+        if (!active(z)) continue;
         const int n = a.n.eval(a.t, z);
         const int npad = n + (n & 1);
         if (i >= npad / 2 || r >= npad - 1) continue;
@@ -182,11 +181,6 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
         }
         if (prev == 0) continue;
         if (sweep >= 1 && mp < sweep - 1 && mq < sweep - 1) continue;
-        if (a.bcls >= 0) {
-          const int* cls = reinterpret_cast<const int*>(bufp(a.t, z, a.bcls));
-          const int mode = cls[n];
-          if (mode == 0 || (mode == 1 && cls[p] == cls[q])) continue;
-        }
         T al = 0, be = 0, ga = 0;
         for (int base = 0; base < m; base += 32 * kChunk) {
           if (base > 0) load_chunk(wp, wq, base, m, lane, x, y);
@@ -243,6 +237,7 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
   if (lane == 0 && flops > 0.0) atomicAdd(&a.t.stat[a.flop_slot], flops);
   if (gthread == 0) {
     for (int z = 0; z < nz; ++z) {
+      if (!active(z)) continue;
       int used = 0;
       bool conv = false;
       for (int s = 0; s < sweeps_done; ++s) {
@@ -251,7 +246,7 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
       }
       int* is = a.t.istat + z * a.t.nis;
       if (used > is[IS_SWEEPS_MAX]) is[IS_SWEEPS_MAX] = used;
-      if (!conv && a.n.eval(a.t, z) > 1) is[IS_NONCONV] += 1;
+      if (a.count_nonconv && !conv && a.n.eval(a.t, z) > 1) is[IS_NONCONV] += 1;
     }
   }
 }
@@ -261,16 +256,46 @@ struct CastArgs {
   Tables t;
   int bsrc, bdst;
   Dim rows, cols;
-  int to_float;   // 1: double -> float, 0: float -> double
+  int to_float;   // 1: double -> float, 0: float -> double, 2: double identity (rows x rows)
 };
+constexpr int kCastExpBias = 4096;
 __global__ void cast_kernel(CastArgs a) {
   const int z = blockIdx.y;
-  const long n = (long)a.rows.eval(a.t, z) * a.cols.eval(a.t, z);
+  const int rows = a.rows.eval(a.t, z);
+  const long n = (long)rows * a.cols.eval(a.t, z);
+  // double -> float copies are scaled by 2^-e (e: binary exponent of max |W|, set by
+  // absmax_exp_kernel), so that the float copy of a matrix of small norm keeps its small
+  // entries out of the float32 subnormal range (the Jacobi rotations are scale-invariant)
+  const int eb = a.t.istat[z * a.t.nis + IS_CAST_EXP];
+  const int sh = eb > 0 ? -(eb - kCastExpBias) : 0;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    if (a.to_float)
-      reinterpret_cast<float*>(bufp(a.t, z, a.bdst))[e] = (float)bufp(a.t, z, a.bsrc)[e];
+    if (a.to_float == 2)
+      bufp(a.t, z, a.bdst)[e] = (e % rows == e / rows) ? 1.0 : 0.0;
+    else if (a.to_float)
+      reinterpret_cast<float*>(bufp(a.t, z, a.bdst))[e] = (float)ldexp(bufp(a.t, z, a.bsrc)[e], sh);
     else
       bufp(a.t, z, a.bdst)[e] = (double)reinterpret_cast<const float*>(bufp(a.t, z, a.bsrc))[e];
+  }
+}
+
+// Binary exponent of max |X| of a rows x cols matrix, biased by kCastExpBias, into
+// IS_CAST_EXP (reset to 0 by the first block row of reset_cast_exp_kernel before).
+__global__ void reset_cast_exp_kernel(Tables t) {
+  const int z = threadIdx.x + blockIdx.x * blockDim.x;
+  if (z < t.nz) t.istat[z * t.nis + IS_CAST_EXP] = 0;
+}
+__global__ void absmax_exp_kernel(CastArgs a) {
+  const int z = blockIdx.y;
+  const long n = (long)a.rows.eval(a.t, z) * a.cols.eval(a.t, z);
+  const double* x = bufp(a.t, z, a.bsrc);
+  double m = 0.0;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[e]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0 && m == m) {
+    int e;
+    frexp(m, &e);
+    atomicMax(&a.t.istat[z * a.t.nis + IS_CAST_EXP], e + kCastExpBias);
   }
 }
 
@@ -307,10 +332,12 @@ __global__ void rank_kernel(RankArgs a) {
   const int n = a.n.eval(a.t, z);
   if (j >= n) return;
   const double* nr = bufp(a.t, z, a.bnrm);
-  const double v = nr[j];
+  // squared norms are >= 0; a NaN sorts last, so that perm stays a permutation
+  auto key = [](double x) { return x == x ? x : -1.0; };
+  const double v = key(nr[j]);
   int rank = 0;
   for (int i = 0; i < n; ++i) {
-    const double u = nr[i];
+    const double u = key(nr[i]);
     rank += (u > v) || (u == v && i < j);
   }
   bufp(a.t, z, a.bsorted)[rank] = v;
@@ -328,7 +355,10 @@ struct TruncArgs {
   int cap;        // 0 = none
   int wslot;      // stat slot for this truncation's discarded weight (-1: none)
   int record;     // 1: final decision (statistics); 0: provisional (bond value only)
-  int ieps;       // -1, or bond id that receives the Eq. eps rank before the cap
+  int ikeep;      // -1, or (final rounding) the bond id of the current bond: when the
+                  // product's rounding gate IS_ROUND is 0 no output bond exceeds chi_out,
+                  // and the SVD keeps that many values (an exact refactorisation)
+  int tslot;      // -1, or stat slot receiving the total sum_j lambda_j^2
 };
 __global__ void __launch_bounds__(1024) truncate_kernel(TruncArgs a) {
   const int z = blockIdx.x;
@@ -362,14 +392,16 @@ __global__ void __launch_bounds__(1024) truncate_kernel(TruncArgs a) {
   __syncthreads();
   if (tid == 0) {
     int k = kbest;
+    if (!(total == total) || total > 1.79e308) atomicExch(&a.t.istat[z * a.t.nis + IS_STATUS], (int)TTM_ERR_NONFINITE);
     if (!(total > 0.0)) k = 1;
     if (a.cap > 0 && k > a.cap) k = a.cap;
+    if (a.ikeep >= 0 && a.t.istat[z * a.t.nis + IS_ROUND] == 0) k = bondv(a.t, z, a.ikeep);
     const int kmax = max(1, min(m, n));
     k = max(1, min(k, kmax));
     double w = 0.0;
     for (int j = n - 1; j >= k; --j) w += s[j];
     a.t.bond[z * a.t.nbd + a.inew] = k;
-    if (a.ieps >= 0) a.t.bond[z * a.t.nbd + a.ieps] = (total > 0.0) ? kbest : 1;
+    if (a.tslot >= 0) a.t.stat[z * a.t.ns + a.tslot] = total;
     if (!a.record) return;
     double* st = a.t.stat + z * a.t.ns;
     st[ST_WSUM] += w;
@@ -380,39 +412,18 @@ __global__ void __launch_bounds__(1024) truncate_kernel(TruncArgs a) {
   }
 }
 
-// Membership of every column in the kept set of a provisional truncation (cls[perm[r]] =
-// (r < k)) and the polish mode of the product in cls[n]: 0 when every column is kept (W V^T
-// = Theta already holds exactly), 1 (kept/dropped pairs only) when the cap clearly decides
-// the kept set, 2 (all pairs) otherwise. The cap decides when the Eq. eps rank exceeds it by
-// a margin and eps is far above the float64 noise of the column norms (a tiny eps would let
-// rounding-level columns pass as kept). Rotations inside the kept or the dropped set leave
-// the truncated tensor W_K V_K^T and the discarded weight ||W_D||_F^2 unchanged.
-struct ClassArgs {
+// Gate of the final rounding (reading A4): IS_ROUND of a product becomes 1 when one of the
+// listed bonds (the output's internal bonds before the rounding) exceeds the cap.
+struct RoundGateArgs {
   Tables t;
-  int bperm, bcls;
-  Dim n;
-  int ik, ieps;  // bond ids: provisional rank (after the cap) and Eq. eps rank
+  int n;          // ids used (<= 32)
+  int ids[32];
   int cap;
-  double eps;
 };
-__global__ void classify_kernel(ClassArgs a) {
-  const int z = blockIdx.y;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = a.n.eval(a.t, z);
-  const int k = bondv(a.t, z, a.ik);
-  int* cls = reinterpret_cast<int*>(bufp(a.t, z, a.bcls));
-  if (r == 0) {
-    const int keps = bondv(a.t, z, a.ieps);
-    int mode = 2;
-    if (k >= n)
-      mode = 0;
-    else if (a.cap > 0 && k == a.cap && a.eps >= 1e-18 && keps >= a.cap + max(8, a.cap / 4))
-      mode = 1;
-    cls[n] = mode;
-  }
-  if (r >= n) return;
-  const int j = reinterpret_cast<const int*>(bufp(a.t, z, a.bperm))[r];
-  cls[j] = (r < k) ? 1 : 0;
+__global__ void round_gate_kernel(RoundGateArgs a) {
+  const int z = blockIdx.x;
+  const int i = threadIdx.x;
+  if (i < a.n && bondv(a.t, z, a.ids[i]) > a.cap) atomicOr(&a.t.istat[z * a.t.nis + IS_ROUND], 1);
 }
 
 // New carriages after a Swap: left[(l, t), j] = W[(l, t), perm[j]] (row-major
@@ -431,6 +442,7 @@ __global__ void swap_gather_kernel(GatherArgs a) {
   if (j >= k) return;
   const int m = Dl * a.d, n = a.d * Dr;
   const int pj = reinterpret_cast<const int*>(bufp(a.t, z, a.bperm))[j];
+  if (pj < 0 || pj >= n) return;  // cannot happen for a permutation; never read outside W
   if (row < m) bufp(a.t, z, a.bleft)[(long)row * k + j] = bufp(a.t, z, a.bw)[row + (long)pj * m];
   if (row < n) bufp(a.t, z, a.bright)[(long)j * n + row] = bufp(a.t, z, a.bv)[row + (long)pj * n];
 }

@@ -37,8 +37,12 @@ int main(void) {
   CHECK(ttm_create(&h, 0, NULL, &opt) == TTM_ERR_INVALID_ARG);
   CHECK(strstr(ttm_last_error(), "eps") != NULL);
   opt.eps = 0.0;
-  opt.prec = TTM_PREC_TF32X3;
-  CHECK(ttm_create(&h, 0, NULL, &opt) == TTM_ERR_UNSUPPORTED);
+  opt.prec = (ttm_precision)1; /* not a precision mode */
+  CHECK(ttm_create(&h, 0, NULL, &opt) == TTM_ERR_INVALID_ARG);
+  opt.prec = TTM_PREC_BF16_SPLIT;
+  opt.split_digits = 9;
+  CHECK(ttm_create(&h, 0, NULL, &opt) == TTM_ERR_INVALID_ARG);
+  opt.split_digits = 0;
   opt.prec = TTM_PREC_FP64;
   opt.f32_block = 5;
   CHECK(ttm_create(&h, 0, NULL, &opt) == TTM_ERR_INVALID_ARG);
@@ -61,15 +65,17 @@ int main(void) {
   FIELD(ttm_options, chi_out); FIELD(ttm_options, max_sweeps); FIELD(ttm_options, use_graph);
   FIELD(ttm_options, check_finite); FIELD(ttm_options, profile_kernels);
   FIELD(ttm_options, f32_passes); FIELD(ttm_options, f32_block);
-  FIELD(ttm_options, polish_kept_dropped); FIELD(ttm_options, reserved1);
+  FIELD(ttm_options, newton_steps); FIELD(ttm_options, split_digits);
   printf("layout ttm_report.sizeof 0 %zu\n", sizeof(ttm_report));
   FIELD(ttm_report, status); FIELD(ttm_report, jacobi_sweeps_max); FIELD(ttm_report, max_bond);
   FIELD(ttm_report, n_swaps); FIELD(ttm_report, n_contracts); FIELD(ttm_report, n_qr);
   FIELD(ttm_report, discarded_weight); FIELD(ttm_report, err_bound); FIELD(ttm_report, norm_out);
   FIELD(ttm_report, flops_counted); FIELD(ttm_report, seconds); FIELD(ttm_report, peak_workspace_bytes);
   FIELD(ttm_report, bond_trace); FIELD(ttm_report, bond_trace_len); FIELD(ttm_report, n_kernel_launches);
-  FIELD(ttm_report, jacobi_launches); FIELD(ttm_report, jacobi_ms); FIELD(ttm_report, jacobi_flops);
-  FIELD(ttm_report, jacobi32_ms); FIELD(ttm_report, jacobi32_flops);
+  FIELD(ttm_report, jacobi_launches); FIELD(ttm_report, gemm_ms); FIELD(ttm_report, newton_residual);
+  FIELD(ttm_report, jacobi32_ms); FIELD(ttm_report, jacobi32_flops); FIELD(ttm_report, n_nonconverged);
+  FIELD(ttm_report, n_frozen_pairs); FIELD(ttm_report, gemm_flops); FIELD(ttm_report, gemm_launches);
+  FIELD(ttm_report, qr_ms); FIELD(ttm_report, n_fallback);
 #undef FIELD
 
   if (failures == 0) printf("c abi check ok\n");

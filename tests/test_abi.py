@@ -66,12 +66,12 @@ def test_option_validation_without_gpu(lib):
     import paper_2410_19747_gb300.binding as b
     h = ctypes.c_void_p()
     for kw, status in ((dict(f32_block=5), -1), (dict(f32_passes=9), -1), (dict(f32_passes=-1), -1),
-                       (dict(polish_kept_dropped=2), -1), (dict(use_graph=1), -9)):
+                       (dict(newton_steps=9), -1), (dict(newton_steps=-1), -1), (dict(use_graph=1), -9)):
         o = b.make_options(**kw)
         assert lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == status, kw
     # accepted options get past validation: without a GPU the next step is a CUDA error
     for kw in (dict(f32_block=8), dict(f32_block=16), dict(f32_passes=1), dict(chi_max=16, chi_out=8),
-               dict(chi_max=0, chi_out=8), dict(polish_kept_dropped=1, chi_max=16)):
+               dict(chi_max=0, chi_out=8), dict(newton_steps=1, chi_max=16)):
         o = b.make_options(**kw)
         st = lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o))
         assert st not in (-1, -9), (kw, st, lib.ttm_last_error())
@@ -92,7 +92,7 @@ def test_planner_schedules_the_final_rounding_without_gpu(lib):
         cap = b.output_capacity(A, B, **kw)
         assert cap >= min(plain, 32 * 2 * 32), kw
     # the kept/dropped polish adds bond ids to the plan but no carriage
-    assert b.output_capacity(A, B, chi_max=32, chi_out=32, polish_kept_dropped=1) == plain
+    assert b.output_capacity(A, B, chi_max=32, chi_out=32, newton_steps=2) == plain
     assert np.isfinite(plain)
 
 
