@@ -73,7 +73,7 @@ def config(args):
             "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
             "precision_mode": prec, "batch": getattr(args, "batch", 1),
             "svd": "one-sided Jacobi, %d float32 passes (%s), then %d float64 Newton steps; GEMMs %s"
-                   % (args.f32_passes or 2, "block width %d" % args.f32_block if args.f32_block else "scalar",
+                   % (args.f32_passes or 2, "block width %d" % args.jacobi_kernel if args.jacobi_kernel else "scalar",
                       getattr(args, "newton_steps", 0) or 3,
                       "on the float64 pipe" if prec == "fp64" else
                       "as %d-digit bf16 products on the tensor cores" % (getattr(args, "split_digits", 0) or 8)),
@@ -414,7 +414,7 @@ def main():
              for a, b in host_pairs]
     Ag, Bg = pairs[0]
     kw = dict(eps=args.eps, chi_max=args.chi, chi_out=args.chi, prec=args.prec, f32_passes=args.f32_passes,
-              f32_block=args.f32_block, newton_steps=args.newton_steps, split_digits=args.split_digits)
+              jacobi_kernel=args.jacobi_kernel, newton_steps=args.newton_steps, split_digits=args.split_digits)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 

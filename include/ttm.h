@@ -97,15 +97,20 @@ typedef struct {
   int32_t profile_kernels;  /* 1: time every GEMM, float32 Jacobi and Householder launch
                                with CUDA events on the handle's stream (fills gemm_ms,
                                jacobi32_ms and qr_ms of the report)                      */
-  int32_t f32_passes;       /* float32 one-sided Jacobi passes of every Swap SVD: 0 = 2
+  int32_t f32_passes;       /* float32 one-sided Jacobi passes of every Swap SVD: 0 = 3
                                (the first stops after 3 sweeps), 1..8 accepted           */
-  int32_t f32_block;        /* float32 passes: 0 = scalar one-sided Jacobi (one grid
-                               barrier per round of column pairs); 8 or 16 = block Jacobi
-                               on blocks of that many columns (one barrier per round of
-                               block pairs)                                              */
+  int32_t jacobi_kernel;    /* kernel of the float32 passes: 0 or 1 = one column per
+                               tournament slot (n - 1 grid barriers per sweep); 2 = two
+                               columns per slot (n/2 - 1 barriers, more work per warp;
+                               m, n <= 1024); 8 or 16 = block Jacobi on blocks of that
+                               many columns                                              */
   int32_t newton_steps;     /* float64 Newton steps that finish every Swap SVD after the
                                float32 passes: 0 = 3, 1..8 accepted                      */
   int32_t split_digits;     /* digits per operand of TTM_PREC_BF16_SPLIT: 0 = 8, 2..8   */
+  int32_t reserved1;        /* must be 0                                                 */
+  int64_t env_budget_bytes; /* ttm_backward: device memory for the stored left
+                               environments; above it only every ceil(sqrt(L))-th one is
+                               kept and the others are recomputed; 0 = 4 GiB            */
 } ttm_options;
 
 /* Filled by ttm_multiply. All fields are host values once the call returns. */
@@ -144,6 +149,13 @@ typedef struct {
                                   (profile_kernels = 1), else 0                            */
   int64_t n_fallback;          /* Swap SVDs whose Newton steps did not reach float64
                                   rounding and were finished by the float64 Jacobi        */
+  int64_t jacobi32_sweeps;     /* float32 Jacobi sweeps run, summed over the SVDs (with the
+                                  scalar kernel; 0 with the others)                        */
+  int32_t *svd_trace;          /* caller array or NULL: 8 int32 per SVD in issue order (the
+                                  Swaps, then the final rounding): m, n, the kept rank k,
+                                  float32 sweeps of passes 0, 1, 2, 1 if the SVD took the
+                                  float64 fallback, 0                                     */
+  int64_t svd_trace_len;       /* in: capacity of svd_trace in SVDs; out: SVDs written     */
 } ttm_report;
 
 /* Creates a handle bound to CUDA device `device` and stream `cuda_stream`

@@ -1,10 +1,10 @@
 """torch.autograd.Function around ttm_backward (argument marshalling only).
 
 TTMProductLoss.apply(handle, kind, nA, nB, *coresA, *coresB, *coresWC) returns the scalar
-<W, A o B> (kind "inner") or ||A o B - C||^2 (kind "sqdist"). The forward pass calls
-ttm_backward once, which returns the value and the gradients w.r.t. every core of A and
-B from the library's environment and adjoint kernels; backward scales them by the
-incoming gradient. W and C receive no gradient.
+<W, A o B> (kind "inner") or ||A o B - C||^2 (kind "sqdist"). The forward pass asks
+ttm_backward for the value only (one environment sweep); the gradients w.r.t. the cores
+of A and B are computed by the library's environment and adjoint kernels when backward
+runs, and scaled by the incoming gradient. W and C receive no gradient.
 """
 
 import torch
@@ -18,17 +18,21 @@ class TTMProductLoss(torch.autograd.Function):
         A = [c.detach().contiguous() for c in cores[:nA]]
         B = [c.detach().contiguous() for c in cores[nA:nA + nB]]
         WC = [c.detach().contiguous() for c in cores[nA + nB:]]
-        need_a = any(c.requires_grad for c in cores[:nA])
-        need_b = any(c.requires_grad for c in cores[nA:nA + nB])
-        val, gA, gB = ttm_backward(handle, kind, A, B, WC, want_a=need_a, want_b=need_b)
+        val, _, _ = ttm_backward(handle, kind, A, B, WC, want_a=False, want_b=False)
+        ctx.handle, ctx.kind = handle, kind
         ctx.nA, ctx.nB, ctx.nWC = nA, nB, len(WC)
-        ctx.gA, ctx.gB = gA, gB
+        ctx.need = (any(c.requires_grad for c in cores[:nA]), any(c.requires_grad for c in cores[nA:nA + nB]))
+        ctx.save_for_backward(*A, *B, *WC)
         return torch.tensor(val, dtype=torch.float64, device=A[0].device)
 
     @staticmethod
     def backward(ctx, gout):
-        ga = [gout * g for g in ctx.gA] if ctx.gA is not None else [None] * ctx.nA
-        gb = [gout * g for g in ctx.gB] if ctx.gB is not None else [None] * ctx.nB
+        saved = ctx.saved_tensors
+        A, B, WC = saved[:ctx.nA], saved[ctx.nA:ctx.nA + ctx.nB], saved[ctx.nA + ctx.nB:]
+        need_a, need_b = ctx.need
+        _, gA, gB = ttm_backward(ctx.handle, ctx.kind, list(A), list(B), list(WC), want_a=need_a, want_b=need_b)
+        ga = [gout * g for g in gA] if gA is not None else [None] * ctx.nA
+        gb = [gout * g for g in gB] if gB is not None else [None] * ctx.nB
         return (None, None, None, None, *ga, *gb, *([None] * ctx.nWC))
 
 

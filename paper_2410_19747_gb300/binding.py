@@ -42,8 +42,9 @@ class c_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("eps", ctypes.c_double), ("chi_max", ctypes.c_int64),
                 ("chi_out", ctypes.c_int64), ("max_sweeps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("check_finite", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
-                ("f32_passes", ctypes.c_int32), ("f32_block", ctypes.c_int32),
-                ("newton_steps", ctypes.c_int32), ("split_digits", ctypes.c_int32)]
+                ("f32_passes", ctypes.c_int32), ("jacobi_kernel", ctypes.c_int32),
+                ("newton_steps", ctypes.c_int32), ("split_digits", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32), ("env_budget_bytes", ctypes.c_int64)]
 
 
 class c_report(ctypes.Structure):
@@ -57,7 +58,9 @@ class c_report(ctypes.Structure):
                 ("newton_residual", ctypes.c_double), ("jacobi32_ms", ctypes.c_double),
                 ("jacobi32_flops", ctypes.c_double), ("n_nonconverged", ctypes.c_int64),
                 ("n_frozen_pairs", ctypes.c_int64), ("gemm_flops", ctypes.c_double),
-                ("gemm_launches", ctypes.c_int64), ("qr_ms", ctypes.c_double), ("n_fallback", ctypes.c_int64)]
+                ("gemm_launches", ctypes.c_int64), ("qr_ms", ctypes.c_double), ("n_fallback", ctypes.c_int64),
+                ("jacobi32_sweeps", ctypes.c_int64), ("svd_trace", ctypes.POINTER(ctypes.c_int32)),
+                ("svd_trace_len", ctypes.c_int64)]
 
 
 _LIB = None
@@ -115,10 +118,10 @@ def _check(status):
 
 
 def make_options(prec="fp64", eps=0.0, chi_max=0, chi_out=0, max_sweeps=0, use_graph=0, profile=0,
-                 f32_passes=0, f32_block=0, newton_steps=0, split_digits=0):
+                 f32_passes=0, jacobi_kernel=0, newton_steps=0, split_digits=0, env_budget_bytes=0):
     return c_options(PREC[prec] if isinstance(prec, str) else int(prec), float(eps), int(chi_max),
                      int(chi_out), int(max_sweeps), int(use_graph), 0, int(profile), int(f32_passes),
-                     int(f32_block), int(newton_steps), int(split_digits))
+                     int(jacobi_kernel), int(newton_steps), int(split_digits), 0, int(env_budget_bytes))
 
 
 class TTDesc:
@@ -180,8 +183,10 @@ class Handle:
             pass
 
 
-def report_dict(r, trace=None):
-    out = {f: getattr(r, f) for f, _ in c_report._fields_ if f != "bond_trace"}
+def report_dict(r, trace=None, svd=None):
+    out = {f: getattr(r, f) for f, _ in c_report._fields_ if f not in ("bond_trace", "svd_trace")}
+    if svd is not None:
+        out["svd_trace"] = [tuple(svd[8 * i + j] for j in range(7)) for i in range(r.svd_trace_len)]
     out["status_name"] = STATUS.get(r.status, r.status)
     if trace is not None:
         out["bond_trace"] = [int(trace[i]) for i in range(r.bond_trace_len)]
@@ -228,11 +233,11 @@ def _shape_out(o, bufs, d):
 
 
 def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                         f32_passes=0, f32_block=0, newton_steps=0, split_digits=0):
+                         f32_passes=0, jacobi_kernel=0, newton_steps=0, split_digits=0):
     """[(A_i, B_i)] -> ([Omega_i], [report_i]) with one batched launch sequence (ttm_multiply_batched)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
-                       profile=profile, f32_passes=f32_passes, f32_block=f32_block,
+                       profile=profile, f32_passes=f32_passes, jacobi_kernel=jacobi_kernel,
                        newton_steps=newton_steps, split_digits=split_digits)
     n = len(pairs)
     da = [TTDesc(A) for A, _ in pairs]
@@ -261,11 +266,11 @@ def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp6
 
 
 def ttm_multiply(handle, A, B, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                 f32_passes=0, f32_block=0, newton_steps=0, split_digits=0):
+                 f32_passes=0, jacobi_kernel=0, newton_steps=0, split_digits=0):
     """Omega = A o B through ttm_multiply. Returns (cores, report)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
-                       profile=profile, f32_passes=f32_passes, f32_block=f32_block,
+                       profile=profile, f32_passes=f32_passes, jacobi_kernel=jacobi_kernel,
                        newton_steps=newton_steps, split_digits=split_digits)
     a, b = TTDesc(A), TTDesc(B)
     o = make_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out)
@@ -276,11 +281,15 @@ def ttm_multiply(handle, A, B, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_s
     outs, keep = _alloc_out(like, a.c.L, cap, 1)
     out = outs[0]
     trace = (ctypes.c_int64 * a.c.L)()
+    nsvd = a.c.L * a.c.L
+    svd = (ctypes.c_int32 * (8 * nsvd))()
     rep = c_report()
     rep.bond_trace = ctypes.cast(trace, ctypes.POINTER(ctypes.c_int64))
     rep.bond_trace_len = a.c.L
+    rep.svd_trace = ctypes.cast(svd, ctypes.POINTER(ctypes.c_int32))
+    rep.svd_trace_len = nsvd
     _check(lib.ttm_multiply(handle.h, ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(out), ctypes.byref(rep)))
-    return _shape_out(out, keep[0], a.c.d), report_dict(rep, trace)
+    return _shape_out(out, keep[0], a.c.d), report_dict(rep, trace, svd)
 
 
 def ttm_inner(handle, X, Y):

@@ -54,6 +54,7 @@ void Engine::qr_move(int c, int& nx, int bl, int& br, int brr) {
   q_elems_ = std::max(q_elems_, (long)m_ub * k_ub);
   vec_elems_ = std::max(vec_elems_, (long)k_ub + 1);
   log_.push_back({SK_QR, bl, br, nbnd, brr});
+  tc_reserve(1, k_ub, d_ * umax(brr), n_ub);            // R merge
   const int out = get_buf();
   note_carriage(bl, nbnd);
   note_carriage(nbnd, brr);
@@ -61,7 +62,7 @@ void Engine::qr_move(int c, int& nx, int bl, int& br, int brr) {
     const Dim m{d_, bl}, n{1, br};
     copy2d(RowToColFn{tab_, c, ws(WS_T), m, n}, 1, m_ub, n_ub);
     QRArgs qa{tab_, ws(WS_T), ws(WS_TAU), ws(WS_R), ws(WS_Q), m, n, nbnd, n_ub, k_ub};
-    timed(2, [&] { coop((void*)householder_kernel, &qa, hs_.coop_qr, (long)Z_ * n_ub, 8); });
+    timed(2, [&] { coop((void*)householder_kernel, &qa, 1, (long)Z_ * n_ub); });
     copy2d(ColToRowFn{tab_, ws(WS_Q), c, m, Dim{1, nbnd}}, 1, m_ub, k_ub);
     gemm(RMergeFn{tab_, ws(WS_R), nx, out, nbnd, br, brr, d_}, 1, k_ub, d_ * umax(brr), n_ub,
          GemmShape{Dim{1, nbnd}, Dim{d_, brr}, Dim{1, br}, 1, 0});
@@ -94,7 +95,12 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
   log_.push_back({kind, bl, bm, br, nbnd});
   note_carriage(bl, nbnd);
   note_carriage(nbnd, br);
+  cur_svd_ = n_trunc_;
   const int wslot = ST_NFIXED + n_trunc_++;
+  // digit workspace of the tensor-core GEMMs below (sized in the planning walk too)
+  tc_reserve(d_ * d_, umax(bl), umax(br), umax(bm));   // Theta
+  tc_reserve(1, m_ub, n_ub, n_ub);                      // W X, W V32
+  tc_reserve(1, n_ub, n_ub, std::max(m_ub, n_ub));      // Grams of W and V, V X
   const int npass = f32_passes();
   const int sw32 = jac_launch_;
   jac_launch_ += npass;
@@ -155,7 +161,7 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
       const int g = take(), mm = take(), xb = take();
       gemm(GramFn{tab_, wb, g, m, n}, 1, n_ub, n_ub, m_ub, GemmShape{n, n, m, 1, 1});
       gemm(GramFn{tab_, vb, mm, n, n}, 1, n_ub, n_ub, n_ub, GemmShape{n, n, n, 1, 1});
-      newton_x(g, mm, xb, n, n_ub, nprov, s == 0 ? 1 : 0, 0, s + 1 == nsteps, -1);
+      newton_x(g, mm, xb, n, n_ub, nprov, 0, s + 1 == nsteps, -1);
       if (tc_) colexp(wb, m, n, n_ub);
       gemm(ThetaVFn{tab_, wb, xb, wo, m, n}, 1, m_ub, n_ub, n_ub, GemmShape{m, n, n, 1, 0},
            tc_ ? ws(WS_TAU) : -1);  // W <- W X
@@ -177,7 +183,7 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
         const int mm = take(), xb = take(), vn = take();
         gemm(PredFn<GramFn>{GramFn{tab_, fv, mm, n, n}, IS_FALLBACK, 1, tab_}, 1, n_ub, n_ub, n_ub,
              GemmShape{n, n, n, 1, 1});
-        newton_x(mm, mm, xb, n, n_ub, nprov, 0, 1, false, IS_FALLBACK);
+        newton_x(mm, mm, xb, n, n_ub, nprov, 1, false, IS_FALLBACK);
         if (tc_) colexp(fw, m, n, n_ub);
         gemm(PredFn<ThetaVFn>{ThetaVFn{tab_, fw, xb, fw2, m, n}, IS_FALLBACK, 1, tab_}, 1, m_ub, n_ub, n_ub,
              GemmShape{m, n, n, 1, 0}, tc_ ? ws(WS_TAU) : -1);
@@ -190,8 +196,9 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
         fv = vn;
       }
       HestArgs h64{tab_, fw, fv, m, n, npad_ub, kPolishSweeps, counters_ + (size_t)sw64 * counter_stride_, 1e-10,
-                   64 * 1.11e-16, fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), 1, IS_FALLBACK};
-      timed(1, [&] { coop((void*)hestenes_kernel<double>, &h64, hs_.coop_hest, pairs); });
+                   64 * 1.11e-16, fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), 1, IS_FALLBACK, -1, nullptr,
+                   0, 0};
+      timed(1, [&] { coop((void*)hestenes_kernel<double>, &h64, 1, pairs); });
       pcopy(fw, wb, m, n, IS_FALLBACK, 1, (long)m_ub * n_ub);
       pcopy(fv, vb, n, n, IS_FALLBACK, 1, (long)n_ub * n_ub);
       if (fv != ws(WS_V0)) fr.push_back(fv);
@@ -219,17 +226,33 @@ void Engine::jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int 
                counters_ + (size_t)slot * counter_stride_,
                16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)),
                pass == 0 ? 64 * 5.96e-8 : 64 * 1.11e-16,
-               fro2_ + (size_t)slot * Z_, 1, ST_JFLOPS32, ws(WS_NRM), pass > 0 ? 1 : 0, -1};
-  if (opt_.f32_block > 0) {
-    const int fb = opt_.f32_block;
+               fro2_ + (size_t)slot * Z_, 1, ST_JFLOPS32, ws(WS_NRM), pass > 0 ? 1 : 0, -1, ST_JSWEEPS32,
+               pass < 3 ? svd_rec(cur_svd_) : nullptr, svd_stride(), SR_SW0 + pass};
+  const int jk = opt_.jacobi_kernel;
+  const bool fits2 = m_ub <= 32 * 32 && n_ub <= kJ4MaxN;
+  if (jk == 2 && !fits2)
+    throw Error(TTM_ERR_UNSUPPORTED, "jacobi_kernel = 2 needs Swap matrices of at most 1024 x 1024");
+  if (jk == 8 || jk == 16) {
+    const int fb = jk;
     const int nblk_ub = (n_ub + fb - 1) / fb;
     const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
     BJacArgs bj{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, sweeps,
                 h32.counters, h32.tol, h32.delta, h32.fro2, ST_JFLOPS32, h32.count_nonconv};
     void* fn = fb == 8 ? (void*)block_jacobi_kernel<8> : (void*)block_jacobi_kernel<16>;
     timed(1, [&] { coop(fn, &bj, bjac_blocks_per_sm(fb), (long)Z_ * (nblk_pad_ub / 2)); });
+  } else if (jk == 2) {
+    const int ns_ub = (n_ub + 1) / 2;
+    const int nsp_ub = ns_ub + (ns_ub & 1);
+    Jac4Args ja{tab_, ws(WS_W32), ws(WS_V32), m, n, nsp_ub, sweeps, h32.counters, h32.tol, h32.delta, h32.fro2,
+                ST_JFLOPS32, h32.count_nonconv};
+    const int rows = (m_ub + 31) / 32;
+    void* fn = rows <= 1 ? (void*)jacobi4_kernel<1> : rows <= 2 ? (void*)jacobi4_kernel<2>
+             : rows <= 4 ? (void*)jacobi4_kernel<4> : rows <= 8 ? (void*)jacobi4_kernel<8>
+             : rows <= 16 ? (void*)jacobi4_kernel<16> : (void*)jacobi4_kernel<32>;
+    const long units = (long)Z_ * (nsp_ub / 2);
+    timed(1, [&] { coop_j4(fn, &ja, units); });
   } else {
-    timed(1, [&] { coop((void*)hestenes_kernel<float>, &h32, hs_.coop_hest32, pairs); });
+    timed(1, [&] { coop((void*)hestenes_kernel<float>, &h32, 1, pairs); });
   }
 }
 
@@ -245,7 +268,8 @@ void Engine::order_and_truncate(int wbuf, Dim m, Dim n, int ibond, int record, i
   dim3 g2(cdiv(n_ub, 256), Z_);
   rank_kernel<<<g2, 256, 0, hs_.stream>>>(ra);
   TTM_CUDA(cudaGetLastError());
-  TruncArgs ta{tab_, ws(WS_SORT), m, n, ibond, opt_.eps, (int)cap, wslot, record, ikeep, tslot};
+  TruncArgs ta{tab_, ws(WS_SORT), m, n, ibond, opt_.eps, (int)cap, wslot, record, ikeep, tslot,
+               record ? svd_rec(cur_svd_) : nullptr, svd_stride()};
   truncate_kernel<<<Z_, 1024, 0, hs_.stream>>>(ta);
   TTM_CUDA(cudaGetLastError());
 }
@@ -403,6 +427,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report>* reps, ttm_tt* outs) {
   (void)opt;
   // Layout of the arena: per product [chain buffers | workspaces], then the tables.
+  n_trunc_planned_ = n_trunc_;
   char* base = (char*)arena;
   size_t off = 0;
   hbuf_.assign((size_t)Z_ * nb_, nullptr);
@@ -439,6 +464,8 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   off = align256(off + (size_t)n_jac * Z_ * sizeof(double));
   d_tc_ = (unsigned char*)(base + off);
   off = align256(off + (size_t)tc_bytes_);
+  svd_log_ = (int*)(base + off);
+  off = align256(off + (size_t)Z_ * std::max(1, n_trunc_) * kSvdRec * sizeof(int));
 
   std::vector<int> hb((size_t)Z_ * nbd, 0);
   for (int id = 0; id < nbd; ++id)
@@ -452,6 +479,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   TTM_CUDA(cudaMemsetAsync(d_istat_, 0, (size_t)Z_ * nis * sizeof(int), st));
   TTM_CUDA(cudaMemsetAsync(counters_, 0, (size_t)n_jac * counter_stride_ * sizeof(int), st));
   TTM_CUDA(cudaMemsetAsync(fro2_, 0, (size_t)n_jac * Z_ * sizeof(double), st));
+  TTM_CUDA(cudaMemsetAsync(svd_log_, 0, (size_t)Z_ * std::max(1, n_trunc_) * kSvdRec * sizeof(int), st));
   tab_ = Tables{d_buf_, d_bond_, d_stat_, d_istat_, nb_, nbd, ns, nis, Z_};
 
   // second walk: launch
@@ -512,6 +540,8 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     ttm_report& r = (*reps)[z];
     const int64_t* user_trace = r.bond_trace;
     const int64_t trace_cap = r.bond_trace_len;
+    int32_t* user_svd = r.svd_trace;
+    const int64_t svd_cap = r.svd_trace_len;
     std::memset(&r, 0, sizeof(r));
     r.status = TTM_OK;
     r.jacobi_sweeps_max = istat[(size_t)z * nis + IS_SWEEPS_MAX];
@@ -554,6 +584,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     r.jacobi32_ms = kind_ms[1];
     r.qr_ms = kind_ms[2];
     r.jacobi32_flops = stat[(size_t)0 * ns + ST_JFLOPS32];
+    r.jacobi32_sweeps = (int64_t)stat[(size_t)z * ns + ST_JSWEEPS32];
     r.gemm_launches = (int64_t)gemm_log_.size();
     double gf = 0.0;
     for (const GemmShape& gs : gemm_log_)
@@ -563,6 +594,15 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
         gf += gs.nbatch * (gs.sym ? M * (N + 1) * K : 2.0 * M * N * K);
       }
     r.gemm_flops = gf;
+    if (user_svd && svd_cap > 0) {
+      const int64_t nrec = std::min<int64_t>(svd_cap, n_trunc_);
+      std::vector<int> tmp((size_t)nrec * kSvdRec);
+      TTM_CUDA(cudaMemcpy(tmp.data(), svd_log_ + (size_t)z * svd_stride(), tmp.size() * sizeof(int),
+                          cudaMemcpyDeviceToHost));
+      for (size_t q = 0; q < tmp.size(); ++q) user_svd[q] = tmp[q];
+      r.svd_trace_len = nrec;
+    }
+    r.svd_trace = user_svd;
     r.bond_trace = (int64_t*)user_trace;
     r.bond_trace_len = 0;
     if (user_trace) {
@@ -624,11 +664,14 @@ static ttm_status check_opts(const ttm_options& o) {
     return set_err(TTM_ERR_UNSUPPORTED, "use_graph and check_finite are not built (must be 0)");
   if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)
     return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
-  if (o.f32_block != 0 && o.f32_block != 8 && o.f32_block != 16)
-    return set_err(TTM_ERR_INVALID_ARG, "f32_block must be 0, 8 or 16");
+  if (o.jacobi_kernel != 0 && o.jacobi_kernel != 1 && o.jacobi_kernel != 2 && o.jacobi_kernel != 8 &&
+      o.jacobi_kernel != 16)
+    return set_err(TTM_ERR_INVALID_ARG, "jacobi_kernel must be 0, 1, 2, 8 or 16");
   if (o.newton_steps < 0 || o.newton_steps > kMaxNewtonSteps)
     return set_err(TTM_ERR_INVALID_ARG, "newton_steps must lie in [0, 8]");
   if (o.max_sweeps < 0 || o.max_sweeps > 1000) return set_err(TTM_ERR_INVALID_ARG, "max_sweeps must lie in [0, 1000]");
+  if (o.reserved1 != 0) return set_err(TTM_ERR_INVALID_ARG, "reserved option field must be 0");
+  if (o.env_budget_bytes < 0) return set_err(TTM_ERR_INVALID_ARG, "env_budget_bytes must be >= 0");
   if (o.split_digits != 0 && (o.split_digits < 2 || o.split_digits > kOzMaxS))
     return set_err(TTM_ERR_INVALID_ARG, "split_digits must be 0 or lie in [2, 8]");
   return TTM_OK;
@@ -665,6 +708,8 @@ static ttm_status multiply_impl(ttm_handle* h, int32_t n, const ttm_tt* A, const
       if (rep) {
         reps[i].bond_trace = rep[i].bond_trace;
         reps[i].bond_trace_len = rep[i].bond_trace_len;
+        reps[i].svd_trace = rep[i].svd_trace;
+        reps[i].svd_trace_len = rep[i].svd_trace_len;
       }
     }
     e.execute(h->s.arena.ptr, h->s.opt, &reps, out);
@@ -967,8 +1012,7 @@ ttm_status ttm_gemm(ttm_handle* h, ttm_precision prec, int64_t M, int64_t N, int
       unsigned char* ws = (unsigned char*)h->s.env_arena.ptr;
       int* err = (int*)(ws + need - 256);
       TTM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-      launch_tc_gemm(st, f, 1, 1, (int)M, (int)N, (int)K, -1, S, ws, err);
-      TTM_CUDA(cudaGetLastError());
+      TTM_CUDA(launch_tc_gemm(st, f, 1, 1, (int)M, (int)N, (int)K, -1, S, ws, err));
       int herr = 0;
       TTM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
       TTM_CUDA(cudaStreamSynchronize(st));

@@ -40,10 +40,17 @@ enum { IS_STATUS = 0, IS_MAX_BOND = 1, IS_SWEEPS_MAX = 2, IS_NONCONV = 3, IS_NFR
        IS_ROUND = 6, IS_CAST_EXP = 7, IS_FALLBACK = 8, IS_NFIXED = 9 };
 // stat slots (the per-truncation weights follow from ST_NFIXED)
 enum { ST_WSUM = 0, ST_WSQRT = 1, ST_NEWTON_RES = 2, ST_JFLOPS32 = 3, ST_NEWTON_CUR = 4, ST_TRACE = 5,
-       ST_JFLOPS = 6, ST_NFIXED = 7 };
+       ST_JFLOPS = 6, ST_JSWEEPS32 = 7, ST_NFIXED = 8 };
 
-// Residual of the last Newton step of an SVD above which it counts as not converged.
-constexpr double kNewtonConverged = 1e-8;
+// Per-SVD diagnostic record (the report's svd_trace): m, n, k, float32 sweeps of passes
+// 0, 1, 2, fallback flag.
+constexpr int kSvdRec = 8;
+enum { SR_M = 0, SR_N = 1, SR_K = 2, SR_SW0 = 3, SR_FALLBACK = 6 };
+
+// Largest correction max(|S_ij|, |E_ij| / 2) of the last Newton step of an SVD for which it
+// counts as converged: the error left after a step is of the order of its correction squared,
+// so 1e-7 leaves couplings and an orthogonality defect near 1e-14.
+constexpr double kNewtonConverged = 1e-7;
 
 // A dimension written as mul * bond[id] (id < 0 means the constant mul).
 struct Dim {

@@ -20,6 +20,7 @@
 #include "ttm_svd.cuh"
 #include "ttm_bjac.cuh"
 #include "ttm_newton.cuh"
+#include "ttm_jac4.cuh"
 #include "ttm_tc.cuh"
 
 namespace ttm {
@@ -89,6 +90,11 @@ class Engine {
   int* counters_ = nullptr;
   double* fro2_ = nullptr;
   int counter_stride_ = 0;  // ints per Jacobi launch
+  int* svd_log_ = nullptr;  // [z][SVD][kSvdRec] per-SVD diagnostics (the report's svd_trace)
+  int cur_svd_ = 0;         // index of the SVD being issued
+  int* svd_rec(int i) const { return svd_log_ ? svd_log_ + (size_t)i * kSvdRec : nullptr; }
+  int svd_stride() const { return std::max(1, n_trunc_planned_) * kSvdRec; }
+  int n_trunc_planned_ = 0;
   int jac_launch_ = 0;
   int* d_bond_ = nullptr;
   double** d_buf_ = nullptr;
@@ -151,6 +157,7 @@ class Engine {
     b += (size_t)Z_ * IS_NFIXED * sizeof(int) + 256;
     b += (size_t)std::max(1, jac_launch_) * Z_ * counter_sweeps() * sizeof(int) + 256;
     b += (size_t)std::max(1, jac_launch_) * Z_ * sizeof(double) + 256;
+    b += (size_t)Z_ * std::max(1, n_trunc_) * kSvdRec * sizeof(int) + 256;
     return b;
   }
   // Sweep counters per product and Jacobi launch: room for the sweep limit of any pass.
@@ -170,19 +177,27 @@ class Engine {
   // C = A B of every (product, batch index) the functor describes: on the float64 pipe, or
   // (tc_) as the exactly sliced bf16 product on the tensor cores (ttm_tc.cuh). kscale_buf:
   // per-K power-of-two exponents that keep a graded A relatively accurate (tensor cores only).
+  // Digit workspace of a tensor-core GEMM with these upper bounds; every GEMM a step may
+  // launch is reserved in both walks (the planning walk launches nothing).
+  void tc_reserve(int nbatch, int M_ub, int N_ub, int K_ub) {
+    if (tc_) tc_bytes_ = std::max(tc_bytes_, (long)tc_ws_bytes((long)Z_ * nbatch, M_ub, N_ub, K_ub, split_digits()));
+  }
   // shape: the realised M x N x K of every batch index (for the flop count of the report).
   template <class F>
   void gemm(const F& f, int nbatch, int M_ub, int N_ub, int K_ub, GemmShape shape, int kscale_buf = -1) {
-    if (tc_) {
-      tc_bytes_ = std::max(tc_bytes_, (long)tc_ws_bytes((long)Z_ * nbatch, M_ub, N_ub, K_ub, split_digits()));
+    if (!launch_) {
+      tc_reserve(nbatch, M_ub, N_ub, K_ub);
+      return;
     }
-    if (!launch_) return;
+    if (tc_ && (size_t)tc_bytes_ < tc_ws_bytes((long)Z_ * nbatch, M_ub, N_ub, K_ub, split_digits()))
+      throw Error(TTM_ERR_WORKSPACE, "internal: a tensor-core GEMM was not reserved in the plan");
     gemm_log_.push_back(shape);
     timed(0, [&] {
       if (tc_) {
-        launch_tc_gemm(hs_.stream, f, Z_, nbatch, M_ub, N_ub, K_ub, kscale_buf, split_digits(), d_tc_,
-                       d_istat_ + IS_STATUS);
-        TTM_CUDA(cudaGetLastError());
+        const cudaError_t e = launch_tc_gemm(hs_.stream, f, Z_, nbatch, M_ub, N_ub, K_ub, kscale_buf,
+                                             split_digits(), d_tc_, d_istat_ + IS_STATUS);
+        if (e != cudaSuccess)
+          throw Error(TTM_ERR_CUDA, std::string("tensor-core GEMM, ") + tc_failed_step() + ": " + cudaGetErrorString(e));
         launches_ += 6;
       } else {
         dim3 grid(cdiv(N_ub, GT), cdiv(M_ub, GT), (unsigned)(Z_ * nbatch));
@@ -201,10 +216,10 @@ class Engine {
     ++launches_;
   }
   // X of a Newton step from G and M (ttm_newton.cuh).
-  void newton_x(int g, int mm, int xb, Dim n, int n_ub, int nprov, int graded_only, int eonly, bool last,
+  void newton_x(int g, int mm, int xb, Dim n, int n_ub, int nprov, int eonly, bool last,
                 int islot_pred) {
     if (!launch_) return;
-    NewtonArgs na{tab_, g, mm, xb, n, ws(WS_SORT), nprov, ST_TRACE, graded_only, eonly,
+    NewtonArgs na{tab_, g, mm, xb, n, ws(WS_SORT), nprov, ST_TRACE, eonly,
                   last ? ST_NEWTON_CUR : -1, last ? IS_NFROZEN : -1, islot_pred};
     dim3 blk(32, 8), grd(cdiv(n_ub, 32), cdiv(n_ub, 8), Z_);
     newton_x_kernel<<<grd, blk, 0, hs_.stream>>>(na);
@@ -248,14 +263,26 @@ class Engine {
     ++launches_;
   }
   // Cooperative launch of 256-thread CTAs with one warp per work item (`units` items per round).
-  // The kernels hand work item i to warp i / gridDim.x of CTA i % gridDim.x, so one CTA per
-  // item (up to full co-residency) spreads a round over as many SMs as it has items: the
-  // float64 pipe of every SM works, instead of a few SMs running eight items each.
-  void coop(void* fn, void* args, int blocks_per_sm, long units, int units_per_cta = 8) {
-    (void)units_per_cta;
+  // The kernels hand work item i to warp i / gridDim.x of CTA i % gridDim.x, so a round with
+  // fewer items than warps still spreads over every SM; blocks_per_sm = 1 keeps the number of
+  // CTAs that meet at each grid-wide barrier at one per SM.
+  void coop(void* fn, void* args, int blocks_per_sm, long units) {
     long blocks = std::max(1L, std::min((long)blocks_per_sm * hs_.num_sms, units));
     void* kargs[] = {args};
     TTM_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(256), kargs, 0, hs_.stream));
+    ++launches_;
+  }
+  // Cooperative launch of the two-column-slot Jacobi: at most one CTA of kJ4Warps warps per
+  // SM (a grid barrier with few arrivals), work items spread over the SMs first.
+  void coop_j4(void* fn, void* args, long units) {
+    const size_t smem = (size_t)kJ4Warps * 4 * kJ4MaxN * sizeof(float);
+    TTM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kJ4Warps * 32, smem));
+    if (occ < 1) throw Error(TTM_ERR_UNSUPPORTED, "two-column Jacobi kernel cannot be made resident");
+    const long blocks = std::max(1L, std::min((long)hs_.num_sms, units));
+    void* kargs[] = {args};
+    TTM_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(kJ4Warps * 32), kargs, smem, hs_.stream));
     ++launches_;
   }
   // co-resident 256-thread CTAs per SM of the block Jacobi kernels (queried on first use)

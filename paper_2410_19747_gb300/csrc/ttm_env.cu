@@ -261,6 +261,55 @@ double env_inner3(HandleState& hs, DeviceArena& ar, const ttm_tt& W_, const ttm_
   return read_scalar(hs, E0);
 }
 
+// Left environments L_0 .. L_L for a backward sweep. When all of them fit the budget they
+// are stored; otherwise only every s-th one is kept (s = ceil(sqrt(L)), checkpoints), and
+// the sweep recomputes a segment of s - 1 environments from its checkpoint when it reaches
+// it: about 2 sqrt(L) environments held at a time for one extra forward sweep of work.
+struct LeftEnvs {
+  int L = 0, s = 1, cur = -1;
+  std::vector<double*> ck, seg;
+  // step(k, E_k, E_{k+1}) computes environment k + 1 from environment k
+  template <class Step>
+  double* get(int k, Step&& step) {
+    if (s == 1) return ck[k];
+    const int c = k / s;
+    if (k % s == 0) return ck[c];
+    if (cur != c) {
+      const int hi = std::min(c * s + s - 1, L);
+      const double* prev = ck[c];
+      for (int j = c * s; j < hi; ++j) {
+        step(j, prev, seg[j - c * s]);
+        prev = seg[j - c * s];
+      }
+      cur = c;
+    }
+    return seg[k % s - 1];
+  }
+};
+
+static size_t env_budget(const HandleState& hs) {
+  return hs.opt.env_budget_bytes > 0 ? (size_t)hs.opt.env_budget_bytes : ((size_t)4 << 30);
+}
+
+// Carves the left environments of sizes esz[0..L] (elements) from cur: all of them when they
+// fit the budget, else checkpoints and one segment buffer of the largest size emax.
+static size_t left_bytes(const std::vector<size_t>& esz, size_t emax, size_t budget, int* s_out) {
+  const int L = (int)esz.size() - 1;
+  size_t all = 0;
+  for (size_t e : esz) all += (e * 8 + 255) & ~(size_t)255;
+  if (all <= budget || L < 4) {
+    *s_out = 1;
+    return all;
+  }
+  int s = 1;
+  while (s * s < L) ++s;
+  size_t b = 0;
+  for (int k = 0; k <= L; k += s) b += (esz[k] * 8 + 255) & ~(size_t)255;
+  b += (size_t)(s - 1) * ((emax * 8 + 255) & ~(size_t)255);
+  *s_out = s;
+  return b;
+}
+
 // Gradient of <W, A o B> w.r.t. every core of A: left environments stored, right ones
 // built on the way back. G may be NULL (value only). Returns the value.
 static double grad3(HandleState& hs, DeviceArena& ar, const TTv& W, const TTv& A, const TTv& B,
@@ -269,25 +318,38 @@ static double grad3(HandleState& hs, DeviceArena& ar, const TTv& W, const TTv& A
   size_t e, t1, t2, p, q;
   env3_sizes(W, A, B, e, t1, t2, p, q);
   std::vector<size_t> esz(L + 1);
-  size_t tot = 0;
-  for (int k = 0; k <= L; ++k) {
-    esz[k] = (size_t)W.D[k] * A.D[k] * B.D[k];
-    tot += (esz[k] * 8 + 255) & ~(size_t)255;
-  }
-  ar.ensure(tot + (2 * e + t1 + t2 + p + q) * 8 + 8192);
+  for (int k = 0; k <= L; ++k) esz[k] = (size_t)W.D[k] * A.D[k] * B.D[k];
+  int sck = 1;
+  const size_t lb = G ? left_bytes(esz, e, env_budget(hs), &sck) : 0;
+  ar.ensure(lb + (4 * e + t1 + t2 + p + q) * 8 + 8192);
   char* cur = (char*)ar.ptr;
-  std::vector<double*> Lenv(L + 1);
-  for (int k = 0; k <= L; ++k) Lenv[k] = carve(cur, esz[k]);
   double *R0 = carve(cur, e), *R1 = carve(cur, e), *T1 = carve(cur, t1), *T2 = carve(cur, t2);
-  double *P = carve(cur, p), *Q = carve(cur, q);
+  double *P = carve(cur, p), *Q = carve(cur, q), *F0 = carve(cur, e), *F1 = carve(cur, e);
+  LeftEnvs lv;
+  lv.L = L;
+  lv.s = sck;
+  if (G) {
+    for (int k = 0; k <= L; k += sck) lv.ck.push_back(carve(cur, esz[k]));
+    for (int j = 0; j + 1 < sck; ++j) lv.seg.push_back(carve(cur, e));
+  }
   EnvRunner r(hs);
-  put_one(hs, Lenv[0]);
-  for (int k = 0; k < L; ++k) env3_step(r, d, Lenv[k], W.at(k), A.at(k), B.at(k), T1, T2, Lenv[k + 1]);
-  const double val = read_scalar(hs, Lenv[L]);
+  auto step = [&](int k, const double* Ein, double* Eout) {
+    env3_step(r, d, Ein, W.at(k), A.at(k), B.at(k), T1, T2, Eout);
+  };
+  // forward sweep: the value, and the stored environments (or checkpoints)
+  put_one(hs, F0);
+  if (G) TTM_CUDA(cudaMemcpyAsync(lv.ck[0], F0, 8, cudaMemcpyDeviceToDevice, hs.stream));
+  for (int k = 0; k < L; ++k) {
+    step(k, F0, F1);
+    std::swap(F0, F1);
+    if (G && (k + 1) % sck == 0)
+      TTM_CUDA(cudaMemcpyAsync(lv.ck[(k + 1) / sck], F0, esz[k + 1] * 8, cudaMemcpyDeviceToDevice, hs.stream));
+  }
+  const double val = read_scalar(hs, F0);
   if (!G) return val;
   put_one(hs, R0);
   for (int k = L - 1; k >= 0; --k) {
-    adjoint3(r, d, Lenv[k], R0, W.at(k), A.at(k), B.at(k), P, Q, (*G)[k], alpha, beta);
+    adjoint3(r, d, lv.get(k, step), R0, W.at(k), A.at(k), B.at(k), P, Q, (*G)[k], alpha, beta);
     if (k > 0) {
       env3_step(r, d, R0, W.at_t(k), A.at_t(k), B.at_t(k), T1, T2, R1);
       std::swap(R0, R1);
@@ -302,11 +364,10 @@ static double grad4(HandleState& hs, DeviceArena& ar, const TTv& A, const TTv& B
                     double alpha, double beta) {
   const int L = A.L, d = A.d;
   std::vector<size_t> esz(L + 1);
-  size_t tot = 0, e = 1, t1 = 1, t2 = 1;
+  size_t e = 1, t1 = 1, t2 = 1;
   for (int k = 0; k <= L; ++k) {
     esz[k] = (size_t)A.D[k] * A.D[k] * B.D[k] * B.D[k];
     e = std::max(e, esz[k]);
-    tot += (esz[k] * 8 + 255) & ~(size_t)255;
   }
   for (int k = 0; k < L; ++k)
     for (int dir = 0; dir < 2; ++dir) {
@@ -315,19 +376,34 @@ static double grad4(HandleState& hs, DeviceArena& ar, const TTv& A, const TTv& B
       t1 = std::max({t1, d * Da * Da * Db * Dbp, d * Da * Dap * Dbp * Dbp});
       t2 = std::max(t2, d * Da * Da * Dbp * Dbp);
     }
-  ar.ensure(tot + (2 * e + t1 + t2) * 8 + 8192);
+  int sck = 1;
+  const size_t lb = G ? left_bytes(esz, e, env_budget(hs), &sck) : 0;
+  ar.ensure(lb + (4 * e + t1 + t2) * 8 + 8192);
   char* cur = (char*)ar.ptr;
-  std::vector<double*> Lenv(L + 1);
-  for (int k = 0; k <= L; ++k) Lenv[k] = carve(cur, esz[k]);
   double *R0 = carve(cur, e), *R1 = carve(cur, e), *T1 = carve(cur, t1), *T2 = carve(cur, t2);
+  double *F0 = carve(cur, e), *F1 = carve(cur, e);
+  LeftEnvs lv;
+  lv.L = L;
+  lv.s = sck;
+  if (G) {
+    for (int k = 0; k <= L; k += sck) lv.ck.push_back(carve(cur, esz[k]));
+    for (int j = 0; j + 1 < sck; ++j) lv.seg.push_back(carve(cur, e));
+  }
   EnvRunner r(hs);
-  put_one(hs, Lenv[0]);
-  for (int k = 0; k < L; ++k) env4_step(r, d, Lenv[k], A.at(k), B.at(k), T1, T2, Lenv[k + 1]);
-  const double val = read_scalar(hs, Lenv[L]);
+  auto step = [&](int k, const double* Ein, double* Eout) { env4_step(r, d, Ein, A.at(k), B.at(k), T1, T2, Eout); };
+  put_one(hs, F0);
+  if (G) TTM_CUDA(cudaMemcpyAsync(lv.ck[0], F0, 8, cudaMemcpyDeviceToDevice, hs.stream));
+  for (int k = 0; k < L; ++k) {
+    step(k, F0, F1);
+    std::swap(F0, F1);
+    if (G && (k + 1) % sck == 0)
+      TTM_CUDA(cudaMemcpyAsync(lv.ck[(k + 1) / sck], F0, esz[k + 1] * 8, cudaMemcpyDeviceToDevice, hs.stream));
+  }
+  const double val = read_scalar(hs, F0);
   if (!G) return val;
   put_one(hs, R0);
   for (int k = L - 1; k >= 0; --k) {
-    adjoint4(r, d, Lenv[k], R0, A.at(k), B.at(k), T1, T2, (*G)[k], 2.0 * alpha, beta);
+    adjoint4(r, d, lv.get(k, step), R0, A.at(k), B.at(k), T1, T2, (*G)[k], 2.0 * alpha, beta);
     if (k > 0) {
       env4_step(r, d, R0, A.at_t(k), B.at_t(k), T1, T2, R1);
       std::swap(R0, R1);

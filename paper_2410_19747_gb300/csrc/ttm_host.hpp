@@ -27,7 +27,7 @@ struct Error : std::runtime_error {
   } while (0)
 
 constexpr int kMaxBond = 8192;         // largest bond the planner accepts
-constexpr int kDefaultF32Passes = 2;   // float32 Jacobi passes of every Swap SVD
+constexpr int kDefaultF32Passes = 3;   // float32 Jacobi passes of every Swap SVD
 constexpr int kMaxF32Passes = 8;
 constexpr int kF32Sweeps = 30;         // sweep limit of the later float32 passes
 constexpr int kDefaultNewtonSteps = 3; // float64 Newton steps after the float32 passes

@@ -21,11 +21,11 @@
 //     step cannot resolve;
 //   - couplings above the float64 noise floor kNewtonFloor sqrt(max(d_i, d_j) trace G);
 //   - |S_ij| <= kNewtonMaxS: a pair nearly degenerate relative to its coupling is left
-//     alone (counted as frozen);
-//   - the first step rotates well-separated pairs only (relative gap above 1/2): these carry
-//     the leakage of the large columns into the small ones that the float32 rotations leave
-//     behind, and removing it first keeps it from showing up as couplings between small
-//     columns.
+//     alone (counted as frozen).
+// The steps need the float32 passes to have resolved every relevant pair to float32
+// accuracy, including the small columns: the float64 apply W <- W V32 of a pass leaks a
+// float32-size part of the large columns into the small ones, and the last float32 pass
+// (whose rotations are tiny) is what removes that leakage before the Newton steps.
 // A step in E-only mode applies the polar correction alone (S = 0). A product whose last
 // step leaves max(|S_ij|, |E_ij| / 2) above kNewtonConverged takes the fallback path of the
 // Swap (float64 one-sided Jacobi from the state before the Newton steps).
@@ -44,7 +44,6 @@ struct NewtonArgs {
   Dim n;
   int bsort, ikprov; // sorted squared column norms and the provisional rank (relevance cut)
   int slot_trace;    // stat slot holding trace G = ||W||_F^2 (from the provisional truncation)
-  int graded_only;   // 1: rotate only pairs with a relative gap above 1/2
   int eonly;         // 1: S = 0 (polar correction of V only)
   int slot_smax;     // stat slot receiving max(|S_ij|, |E_ij| / 2) over the product (-1: none)
   int islot_frozen;  // istat slot counting the pairs left unrotated (-1: none)
@@ -87,8 +86,7 @@ __global__ void newton_x_kernel(NewtonArgs a) {
           const double dcut = bufp(a.t, z, a.bsort)[max(0, min(kp, n) - 1)];
           const double tr = a.t.stat[z * a.t.ns + a.slot_trace];
           const double num = 0.5 * e * (di + dj) - g, den = di - dj;
-          const bool relevant = dmax >= kNewtonRelevance * dcut && fabs(num) > kNewtonFloor * sqrt(dmax * tr) &&
-                                (!a.graded_only || fabs(den) > 0.5 * dmax);
+          const bool relevant = dmax >= kNewtonRelevance * dcut && fabs(num) > kNewtonFloor * sqrt(dmax * tr);
           if (relevant) {
             if (fabs(num) <= kNewtonMaxS * fabs(den))
               s = num / den;

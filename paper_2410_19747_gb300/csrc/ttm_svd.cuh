@@ -38,6 +38,9 @@ struct HestArgs {
   int bmark;         // workspace of n ints: last sweep in which each column was rotated
   int count_nonconv; // 1: a product that hits max_sweeps counts in IS_NONCONV
   int islot_pred;    // -1, or istat slot: only products whose slot is non-zero take part
+  int sweep_slot;    // -1, or stat slot accumulating the sweeps run per product
+  int* svd_log;      // nullptr, or this SVD's record of product 0 (stride svd_stride per product)
+  int svd_stride, svd_field;
 };
 
 template <typename T>
@@ -247,6 +250,8 @@ __global__ void __launch_bounds__(256) hestenes_kernel(HestArgs a) {
       int* is = a.t.istat + z * a.t.nis;
       if (used > is[IS_SWEEPS_MAX]) is[IS_SWEEPS_MAX] = used;
       if (a.count_nonconv && !conv && a.n.eval(a.t, z) > 1) is[IS_NONCONV] += 1;
+      if (a.sweep_slot >= 0) a.t.stat[z * a.t.ns + a.sweep_slot] += used;
+      if (a.svd_log) a.svd_log[(long)z * a.svd_stride + a.svd_field] = used;
     }
   }
 }
@@ -359,6 +364,8 @@ struct TruncArgs {
                   // product's rounding gate IS_ROUND is 0 no output bond exceeds chi_out,
                   // and the SVD keeps that many values (an exact refactorisation)
   int tslot;      // -1, or stat slot receiving the total sum_j lambda_j^2
+  int* svd_log;   // nullptr, or this SVD's record of product 0 (stride svd_stride per product)
+  int svd_stride;
 };
 __global__ void __launch_bounds__(1024) truncate_kernel(TruncArgs a) {
   const int z = blockIdx.x;
@@ -409,6 +416,13 @@ __global__ void __launch_bounds__(1024) truncate_kernel(TruncArgs a) {
     if (a.wslot >= 0) st[a.wslot] = w;
     int* is = a.t.istat + z * a.t.nis;
     if (k > is[IS_MAX_BOND]) is[IS_MAX_BOND] = k;
+    if (a.svd_log) {
+      int* rec = a.svd_log + (long)z * a.svd_stride;
+      rec[SR_M] = m;
+      rec[SR_N] = n;
+      rec[SR_K] = k;
+      rec[SR_FALLBACK] = is[IS_FALLBACK];
+    }
   }
 }
 

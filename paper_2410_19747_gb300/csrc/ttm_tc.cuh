@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzArgs<F> a, int
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   const uint32_t tcols = oz_tmem_cols(S);
+  __syncwarp();     // warp 0 reconverges after thread 0's barrier set-up (alloc is warp-collective)
   if (warp == 0) {  // TMEM: S accumulators of 64 float32 columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(tcols)
@@ -398,8 +399,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzArgs<F> a, int
     for (int j = 0; j < kOzTN; ++j) acc[j] = 0.0;
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
-      if (!mbar_wait(smem_u32(&bars[4]), kb & 1, kOzWaitNs)) {
-        atomicExch(&s_abort, 1);
+      // one lane waits, the warp reconverges before the warp-collective tcgen05.ld
+      int got = lane == 0 ? (mbar_wait(smem_u32(&bars[4]), kb & 1, kOzWaitNs) ? 1 : 0) : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      __syncwarp();
+      if (!got) {
+        if (lane == 0) atomicExch(&s_abort, 1);
         ok = false;
         break;
       }
@@ -415,23 +420,25 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzArgs<F> a, int
         }
       }
       tc_fence_before();
+      __syncwarp();
       mbar_arrive(smem_u32(&bars[5]));
     }
     if (ok && gr < g.M) {
       const int* eA = a.w.ea + (long)zb * a.w.e_stride;
       const int* eB = a.w.eb + (long)zb * a.w.e_stride;
       const int er = eA[gr];
-#pragma unroll 4
-      for (int j = 0; j < kOzTN; ++j) {
+#pragma unroll
+      for (int j = 0; j < kOzTN; ++j) {  // fully unrolled: acc stays in registers
         const int gc = n0 + j;
-        if (gc >= g.N) break;
-        const int ec = eB[gc];
-        double v = 0.0;
-        if (er != kOzExpNone && ec != kOzExpNone) v = ldexp(acc[j], er + ec);
-        double* c = g.C.p + (long)gr * g.C.rs + (long)gc * g.C.cs;
-        v *= g.alpha;
-        if (g.beta != 0.0) v = fma(g.beta, *c, v);
-        *c = v;
+        if (gc < g.N) {
+          const int ec = eB[gc];
+          double v = 0.0;
+          if (er != kOzExpNone && ec != kOzExpNone) v = ldexp(acc[j], er + ec);
+          double* c = g.C.p + (long)gr * g.C.rs + (long)gc * g.C.cs;
+          v *= g.alpha;
+          if (g.beta != 0.0) v = fma(g.beta, *c, v);
+          *c = v;
+        }
       }
     }
   }
@@ -447,6 +454,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzArgs<F> a, int
 // ---------------------------------------------------------------- host side
 inline long oz_cdiv(long a, long b) { return (a + b - 1) / b; }
 
+// Kernel of launch_tc_gemm that last reported an error (for the error message).
+inline const char*& tc_failed_step() {
+  static thread_local const char* step = "";
+  return step;
+}
+
 // Digit workspace of one launch of nprob problems with the given upper bounds.
 inline size_t tc_ws_bytes(long nprob, int M_ub, int N_ub, int K_ub, int S) {
   const long mpad = oz_cdiv(M_ub, kOzTM) * kOzTM, npad = oz_cdiv(N_ub, kOzTN) * kOzTN;
@@ -458,7 +471,7 @@ inline size_t tc_ws_bytes(long nprob, int M_ub, int N_ub, int K_ub, int S) {
 // Exponents, digits and the tensor-core product of every (z, batch) problem of the functor.
 // ws: tc_ws_bytes(nz * nbatch, ...) bytes of device memory; err: int set on a timeout.
 template <class F>
-void launch_tc_gemm(cudaStream_t st, const F& f, int nz, int nbatch, int M_ub, int N_ub, int K_ub, int kscale_buf,
+cudaError_t launch_tc_gemm(cudaStream_t st, const F& f, int nz, int nbatch, int M_ub, int N_ub, int K_ub, int kscale_buf,
                     int S, unsigned char* ws, int* err) {
   const long mpad = oz_cdiv(M_ub, kOzTM) * kOzTM, npad = oz_cdiv(N_ub, kOzTN) * kOzTN;
   const long kpad = oz_cdiv(K_ub > 0 ? K_ub : 1, kOzKC) * kOzKC;
@@ -478,17 +491,32 @@ void launch_tc_gemm(cudaStream_t st, const F& f, int nz, int nbatch, int M_ub, i
   w.kscale_buf = kscale_buf;
   OzArgs<F> oa{f, nbatch, w};
   const long ne = 2 * nprob * e_ints;
+  // every launch is checked at once: the caller gets the first failing step
+  const char*& step = tc_failed_step();
+  step = "fill_int_kernel";
   fill_int_kernel<<<(unsigned)oz_cdiv(ne, 256), 256, 0, st>>>(w.ea, ne, kOzExpNone);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  step = "oz_exp_kernel";
   const dim3 blk(32, 8);
   oz_exp_kernel<F><<<dim3((unsigned)oz_cdiv(K_ub, 32), (unsigned)oz_cdiv(M_ub, 32), (unsigned)nprob), blk, 0, st>>>(oa, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   oz_exp_kernel<F><<<dim3((unsigned)oz_cdiv(K_ub, 32), (unsigned)oz_cdiv(N_ub, 32), (unsigned)nprob), blk, 0, st>>>(oa, 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  step = "oz_slice_kernel";
   oz_slice_kernel<F, kOzTM><<<dim3((unsigned)(kpad / 32), (unsigned)(mpad / 32), (unsigned)nprob), blk, 0, st>>>(
       oa, 0, (int)mpad, (int)kpad);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   oz_slice_kernel<F, kOzTN><<<dim3((unsigned)(kpad / 32), (unsigned)(npad / 32), (unsigned)nprob), blk, 0, st>>>(
       oa, 1, (int)npad, (int)kpad);
-  cudaFuncSetAttribute(oz_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz_smem_bytes(kOzMaxS));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(oz_gemm_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                oz_smem_bytes(kOzMaxS))) != cudaSuccess)
+    return e;
+  step = "oz_gemm_kernel";
   oz_gemm_kernel<F><<<dim3((unsigned)(npad / kOzTN), (unsigned)(mpad / kOzTM), (unsigned)nprob), kOzThreads,
                       oz_smem_bytes(S), st>>>(oa, (int)mpad, (int)npad, (int)kpad);
+  return cudaGetLastError();
 }
 
 }  // namespace ttm

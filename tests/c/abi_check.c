@@ -44,9 +44,9 @@ int main(void) {
   CHECK(ttm_create(&h, 0, NULL, &opt) == TTM_ERR_INVALID_ARG);
   opt.split_digits = 0;
   opt.prec = TTM_PREC_FP64;
-  opt.f32_block = 5;
+  opt.jacobi_kernel = 5;
   CHECK(ttm_create(&h, 0, NULL, &opt) == TTM_ERR_INVALID_ARG);
-  opt.f32_block = 0;
+  opt.jacobi_kernel = 0;
 
   /* host-side planning: a two-site product of bond-2 trains */
   A.L = 2; A.d = 2; A.on_host = 1; A.reserved = 0; A.bonds = bA; A.cores = coresA;
@@ -64,8 +64,9 @@ int main(void) {
   FIELD(ttm_options, prec); FIELD(ttm_options, eps); FIELD(ttm_options, chi_max);
   FIELD(ttm_options, chi_out); FIELD(ttm_options, max_sweeps); FIELD(ttm_options, use_graph);
   FIELD(ttm_options, check_finite); FIELD(ttm_options, profile_kernels);
-  FIELD(ttm_options, f32_passes); FIELD(ttm_options, f32_block);
+  FIELD(ttm_options, f32_passes); FIELD(ttm_options, jacobi_kernel);
   FIELD(ttm_options, newton_steps); FIELD(ttm_options, split_digits);
+  FIELD(ttm_options, reserved1); FIELD(ttm_options, env_budget_bytes);
   printf("layout ttm_report.sizeof 0 %zu\n", sizeof(ttm_report));
   FIELD(ttm_report, status); FIELD(ttm_report, jacobi_sweeps_max); FIELD(ttm_report, max_bond);
   FIELD(ttm_report, n_swaps); FIELD(ttm_report, n_contracts); FIELD(ttm_report, n_qr);
@@ -76,6 +77,7 @@ int main(void) {
   FIELD(ttm_report, jacobi32_ms); FIELD(ttm_report, jacobi32_flops); FIELD(ttm_report, n_nonconverged);
   FIELD(ttm_report, n_frozen_pairs); FIELD(ttm_report, gemm_flops); FIELD(ttm_report, gemm_launches);
   FIELD(ttm_report, qr_ms); FIELD(ttm_report, n_fallback);
+  FIELD(ttm_report, jacobi32_sweeps); FIELD(ttm_report, svd_trace); FIELD(ttm_report, svd_trace_len);
 #undef FIELD
 
   if (failures == 0) printf("c abi check ok\n");

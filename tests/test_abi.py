@@ -65,12 +65,12 @@ def test_option_validation_without_gpu(lib):
     import ctypes
     import paper_2410_19747_gb300.binding as b
     h = ctypes.c_void_p()
-    for kw, status in ((dict(f32_block=5), -1), (dict(f32_passes=9), -1), (dict(f32_passes=-1), -1),
+    for kw, status in ((dict(jacobi_kernel=5), -1), (dict(f32_passes=9), -1), (dict(f32_passes=-1), -1),
                        (dict(newton_steps=9), -1), (dict(newton_steps=-1), -1), (dict(use_graph=1), -9)):
         o = b.make_options(**kw)
         assert lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == status, kw
     # accepted options get past validation: without a GPU the next step is a CUDA error
-    for kw in (dict(f32_block=8), dict(f32_block=16), dict(f32_passes=1), dict(chi_max=16, chi_out=8),
+    for kw in (dict(jacobi_kernel=8), dict(jacobi_kernel=16), dict(f32_passes=1), dict(chi_max=16, chi_out=8),
                dict(chi_max=0, chi_out=8), dict(newton_steps=1, chi_max=16)):
         o = b.make_options(**kw)
         st = lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o))

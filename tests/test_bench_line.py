@@ -23,7 +23,7 @@ def fake_report(**over):
 
 def args(**over):
     a = dict(gpus=1, steps=1, warmup=3, impl="ours", chi=512, L=30, eps=1e-14, prec="fp64",
-             no_cpu_baseline=False, e2e_steps=1, f32_passes=0, f32_block=0, batch=1, newton_steps=0,
+             no_cpu_baseline=False, e2e_steps=1, f32_passes=0, jacobi_kernel=0, batch=1, newton_steps=0,
              split_digits=0, time_budget=1500.0)
     a.update(over)
     return types.SimpleNamespace(**a)

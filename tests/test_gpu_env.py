@@ -160,3 +160,66 @@ def test_env_full_size_config5_inner(h):
         gk = gA[k].cpu().numpy()
         g = float(np.sum(gk * D))
         assert abs(g - fd) <= 1e-9 * (abs(fd) + np.linalg.norm(gk) * np.linalg.norm(D)) + 1e-12
+
+
+@pytest.mark.parametrize("kind", ["inner", "sqdist"])
+def test_backward_recomputed_environments_equal_stored(kind):
+    """Below the environment budget only every ceil(sqrt(L))-th left environment is kept and the
+    others are recomputed on the way back: the same kernels on the same inputs, so the
+    gradients are identical to those of the stored sweep."""
+    import paper_2410_19747_gb300 as pkg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    L, d = 16, 2
+    A = dev(ttgen.rand_tt(L, d, 8, 61))
+    B = dev(ttgen.rand_tt(L, d, 6, 62))
+    W = dev(ttgen.rand_tt(L, d, 7, 63))
+    hs, hc = pkg.Handle(0), pkg.Handle(0, env_budget_bytes=4096)
+    try:
+        v0, a0, b0 = pkg.ttm_backward(hs, kind, A, B, W)
+        v1, a1, b1 = pkg.ttm_backward(hc, kind, A, B, W)
+    finally:
+        hs.close()
+        hc.close()
+    assert v0 == v1
+    for x, y in zip(a0 + b0, a1 + b1):
+        assert torch.equal(x, y)
+
+
+def test_sqdist_config5_shape_with_recomputed_environments():
+    """||A o B - C||^2 at L = 20, d = 4 (config 5) with chi = 24, the four-layer environments
+    recomputed from checkpoints: the value against the oracle's environments, and directional
+    derivatives of every third core against central differences of the oracle's value (the
+    loss is quadratic in each core, so the difference quotient is exact up to rounding)."""
+    import paper_2410_19747_gb300 as pkg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    L, d, chi = 20, 4, 24
+    A = unit(ttgen.rand_tt(L, d, chi, 5021, canon="left"))
+    B = unit(ttgen.rand_tt(L, d, chi, 5022, canon="left"))
+    C = unit(ttgen.rand_tt(L, d, chi, 5023, canon="left"))
+    C[-1] = C[-1] * 1e-3
+    h = pkg.Handle(0, env_budget_bytes=1 << 20)
+    try:
+        val, gA, gB = pkg.ttm_backward(h, "sqdist", dev(A), dev(B), dev(C))
+    finally:
+        h.close()
+    ref = ott.sqdist_via_environments(A, B, C)
+    assert abs(val - ref) <= 1e-12 * max(1.0, abs(ref))
+    rng = np.random.default_rng(9)
+    for k in range(0, L, 3):
+        for side, T, G in (("A", A, gA), ("B", B, gB)):
+            D = rng.standard_normal(T[k].shape)
+            tp = [c.copy() for c in T]
+            tm = [c.copy() for c in T]
+            tp[k] = tp[k] + 1e-3 * D
+            tm[k] = tm[k] - 1e-3 * D
+            if side == "A":
+                fd = (ott.sqdist_via_environments(tp, B, C) - ott.sqdist_via_environments(tm, B, C)) / 2e-3
+            else:
+                fd = (ott.sqdist_via_environments(A, tp, C) - ott.sqdist_via_environments(A, tm, C)) / 2e-3
+            gk = G[k].cpu().numpy()
+            g = float(np.sum(gk * D))
+            assert abs(g - fd) <= 1e-8 * (abs(fd) + np.linalg.norm(gk) * np.linalg.norm(D)) + 1e-12, (side, k, g, fd)

@@ -38,7 +38,7 @@ def _dev(cores):
     return [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in cores]
 
 
-def _noalloc(pkg, lib, A, B, **opts):
+def _noalloc(pkg, lib, A, B, fill=None, **opts):
     from paper_2410_19747_gb300 import binding as b
     Ad, Bd = _dev(A), _dev(B)
     a, bb = b.TTDesc(Ad), b.TTDesc(Bd)
@@ -47,6 +47,10 @@ def _noalloc(pkg, lib, A, B, **opts):
     assert cap > 0
     L, d = len(A), A[0].shape[1]
     bufs = [torch.empty(cap, dtype=torch.float64, device="cuda") for _ in range(L)]
+    if fill is not None:
+        for t in bufs:
+            t.fill_(fill)
+        torch.cuda.synchronize()
     bonds = (ctypes.c_int64 * (L + 1))()
     ptrs = (ctypes.c_void_p * L)(*[t.data_ptr() for t in bufs])
     out = b.c_tt(L, 0, 0, 0, bonds, ptrs)
@@ -86,6 +90,9 @@ def test_noalloc_refuses_products_beyond_its_array(env):
     pkg, lib, h = env
     A = ttgen.rand_tt(20, 2, 256, 7, canon="left")
     B = ttgen.rand_tt(20, 2, 256, 8, canon="left")
-    st, out, bufs = _noalloc(pkg, lib, A, B, chi_max=256, chi_out=256)
+    st, out, bufs = _noalloc(pkg, lib, A, B, fill=-7.25, chi_max=256, chi_out=256)
     assert st == -4   # TTM_ERR_WORKSPACE
     assert b"workspace" in lib.ttm_last_error()
+    torch.cuda.synchronize()
+    for t in bufs:    # refused before any GPU work: the caller's output buffers are untouched
+        assert bool((t == -7.25).all())
