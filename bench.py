@@ -25,6 +25,7 @@ import time
 
 import numpy as np
 
+T_START = time.monotonic()   # the --time-budget deadline counts from process start
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -32,6 +33,7 @@ METRIC = "TTM products/s + TFLOP/s at chi=512,d=2,L=30; mixed vs FP64 at rel err
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz = 1.259
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12  # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz = 80.5
 L2_BYTES = 129 * 2 ** 20
+CPU_BASELINE_S = 40.0   # allowance for the CPU baseline leg in the --time-budget projection
 
 
 def parse():
@@ -51,10 +53,11 @@ def parse():
     p.add_argument("--split-digits", type=int, default=0, help="digits of bf16_split (0: library default)")
     p.add_argument("--batch", type=int, default=1,
                    help="independent products per step, multiplied in one ttm_multiply_batched call")
-    p.add_argument("--f32-block", type=int, default=0, choices=[0, 8, 16],
-                   help="block width of the float32 Jacobi (0: scalar kernel, the default)")
+    p.add_argument("--jacobi-kernel", type=int, default=0, choices=[0, 1, 2, 3, 8, 16],
+                   help="kernel of the float32 Jacobi passes (0: library default)")
     p.add_argument("--time-budget", type=float, default=1500.0,
-                   help="seconds of timed steps after which no further step is started")
+                   help="seconds from process start by which the run should end: no timed step is "
+                        "started that would end (with the e2e step and the CPU baseline) after it")
     return p.parse_args()
 
 
@@ -73,7 +76,9 @@ def config(args):
             "L": args.L, "d": 2, "chi": args.chi, "eps": args.eps, "chi_out": args.chi,
             "precision_mode": prec, "batch": getattr(args, "batch", 1),
             "svd": "one-sided Jacobi, %d float32 passes (%s), then %d float64 Newton steps; GEMMs %s"
-                   % (args.f32_passes or 2, "block width %d" % args.jacobi_kernel if args.jacobi_kernel else "scalar",
+                   % (args.f32_passes or 3, {0: "default kernel", 1: "scalar kernel", 2: "two-column kernel",
+                                             3: "resident-block kernel", 8: "Gram block 8",
+                                             16: "Gram block 16"}[args.jacobi_kernel],
                       getattr(args, "newton_steps", 0) or 3,
                       "on the float64 pipe" if prec == "fp64" else
                       "as %d-digit bf16 products on the tensor cores" % (getattr(args, "split_digits", 0) or 8)),
@@ -435,9 +440,12 @@ def main():
     stopped = False
     with ClockSampler(dev.index) as clk:
         for q in range(args.steps):
-            # no step is started that would end past the budget (the ranks agree on the decision)
+            # no step is started that would end past the budget, counting the e2e steps and the
+            # CPU baseline still to come (the ranks agree on the decision)
             if q > 0:
-                proj = max_over_ranks(dist, sum(dts) + sum(dts) / len(dts), dev)
+                mean = sum(dts) / len(dts)
+                rest = mean * (1 + args.e2e_steps) + (0.0 if args.no_cpu_baseline else CPU_BASELINE_S + 20.0)
+                proj = max_over_ranks(dist, time.monotonic() - T_START + rest, dev)
                 if proj > args.time_budget:
                     stopped = True
                     break
@@ -483,7 +491,8 @@ def main():
                          clk.summary())
         if stopped:
             line["steps_requested"] = args.steps
-            line["stopped_early"] = "the next step would have ended after --time-budget %.0f s" % args.time_budget
+            line["stopped_early"] = ("the next step would have ended the run after --time-budget %.0f s "
+                                     "(counted from process start)" % args.time_budget)
         flops = float(np.mean([r["flops_counted"] for r in reps]))
         if not args.no_cpu_baseline:
             A, B = host_pairs[0]

@@ -96,14 +96,17 @@ typedef struct {
   int32_t check_finite;     /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
   int32_t profile_kernels;  /* 1: time every GEMM, float32 Jacobi and Householder launch
                                with CUDA events on the handle's stream (fills gemm_ms,
-                               jacobi32_ms and qr_ms of the report)                      */
+                               jacobi32_ms, jacobi64_ms and qr_ms of the report)          */
   int32_t f32_passes;       /* float32 one-sided Jacobi passes of every Swap SVD: 0 = 3
                                (the first stops after 3 sweeps), 1..8 accepted           */
-  int32_t jacobi_kernel;    /* kernel of the float32 passes: 0 or 1 = one column per
+  int32_t jacobi_kernel;    /* kernel of the float32 passes: 0 = 3 when the Swap matrix
+                               has at most 1024 rows, else 1; 1 = one column per
                                tournament slot (n - 1 grid barriers per sweep); 2 = two
-                               columns per slot (n/2 - 1 barriers, more work per warp;
-                               m, n <= 1024); 8 or 16 = block Jacobi on blocks of that
-                               many columns                                              */
+                               columns per slot (n/2 - 1 barriers; m, n <= 1024); 3 =
+                               blocks of 8 columns held in shared memory, all pairs of a
+                               block pair per CTA (about n/8 barriers; m <= 1024); 8 or
+                               16 = Gram-based block Jacobi on blocks of that many
+                               columns                                                   */
   int32_t newton_steps;     /* float64 Newton steps that finish every Swap SVD after the
                                float32 passes: 0 = 3, 1..8 accepted                      */
   int32_t split_digits;     /* digits per operand of TTM_PREC_BF16_SPLIT: 0 = 8, 2..8   */
@@ -149,13 +152,15 @@ typedef struct {
                                   (profile_kernels = 1), else 0                            */
   int64_t n_fallback;          /* Swap SVDs whose Newton steps did not reach float64
                                   rounding and were finished by the float64 Jacobi        */
-  int64_t jacobi32_sweeps;     /* float32 Jacobi sweeps run, summed over the SVDs (with the
-                                  scalar kernel; 0 with the others)                        */
+  int64_t jacobi32_sweeps;     /* float32 Jacobi sweeps run, summed over the SVDs (scalar
+                                  and resident-block kernels; 0 with the others)          */
   int32_t *svd_trace;          /* caller array or NULL: 8 int32 per SVD in issue order (the
                                   Swaps, then the final rounding): m, n, the kept rank k,
                                   float32 sweeps of passes 0, 1, 2, 1 if the SVD took the
                                   float64 fallback, 0                                     */
   int64_t svd_trace_len;       /* in: capacity of svd_trace in SVDs; out: SVDs written     */
+  double jacobi64_ms;          /* device time of the float64 Jacobi of the fallback
+                                  (profile_kernels = 1), else 0                            */
 } ttm_report;
 
 /* Creates a handle bound to CUDA device `device` and stream `cuda_stream`

@@ -60,7 +60,7 @@ class c_report(ctypes.Structure):
                 ("n_frozen_pairs", ctypes.c_int64), ("gemm_flops", ctypes.c_double),
                 ("gemm_launches", ctypes.c_int64), ("qr_ms", ctypes.c_double), ("n_fallback", ctypes.c_int64),
                 ("jacobi32_sweeps", ctypes.c_int64), ("svd_trace", ctypes.POINTER(ctypes.c_int32)),
-                ("svd_trace_len", ctypes.c_int64)]
+                ("svd_trace_len", ctypes.c_int64), ("jacobi64_ms", ctypes.c_double)]
 
 
 _LIB = None

@@ -198,7 +198,15 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
       HestArgs h64{tab_, fw, fv, m, n, npad_ub, kPolishSweeps, counters_ + (size_t)sw64 * counter_stride_, 1e-10,
                    64 * 1.11e-16, fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), 1, IS_FALLBACK, -1, nullptr,
                    0, 0};
-      timed(1, [&] { coop((void*)hestenes_kernel<double>, &h64, 1, pairs); });
+      if (m_ub <= kJrMaxRows) {  // the resident-block kernel on all pairs of the fallback products
+        const int nblk_ub = (n_ub + kJrB - 1) / kJrB;
+        const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
+        JResArgs j64{tab_, fw, fv, m, n, nblk_pad_ub, kPolishSweeps, h64.counters, h64.tol, h64.delta, h64.fro2,
+                     ST_JFLOPS, ws(WS_NRM), 1, -1, nullptr, 0, 0, 0, IS_FALLBACK};
+        timed(3, [&] { jacobi_res<double>(j64, m_ub, nblk_pad_ub); });
+      } else {
+        timed(3, [&] { coop((void*)hestenes_kernel<double>, &h64, 1, pairs); });
+      }
       pcopy(fw, wb, m, n, IS_FALLBACK, 1, (long)m_ub * n_ub);
       pcopy(fv, vb, n, n, IS_FALLBACK, 1, (long)n_ub * n_ub);
       if (fv != ws(WS_V0)) fr.push_back(fv);
@@ -216,9 +224,10 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
   return nbnd;
 }
 
-// One float32 one-sided Jacobi pass on the W32 workspace (V32 starts at I): the scalar kernel
-// (one grid barrier per round of column pairs) or the block kernel (one per round of block
-// pairs). Pass 0 stops at an absolute floor at float32 rounding of ||W||, later passes at
+// One float32 one-sided Jacobi pass on the W32 workspace (V32 starts at I): by default the
+// resident-block kernel (ttm_jres.cuh; one grid barrier per round of block pairs) when the
+// columns have at most 1024 rows, else the scalar kernel (one grid barrier per round of
+// column pairs); jacobi_kernel selects one explicitly. Pass 0 stops at an absolute floor at float32 rounding of ||W||, later passes at
 // float64 rounding.
 void Engine::jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int npad_ub, long pairs,
                       int sweeps) {
@@ -226,10 +235,21 @@ void Engine::jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int 
                counters_ + (size_t)slot * counter_stride_,
                16 * 5.96e-8 * std::sqrt((double)std::max(m_ub, 1)),
                pass == 0 ? 64 * 5.96e-8 : 64 * 1.11e-16,
-               fro2_ + (size_t)slot * Z_, 1, ST_JFLOPS32, ws(WS_NRM), pass > 0 ? 1 : 0, -1, ST_JSWEEPS32,
+               fro2_ + (size_t)slot * Z_, 1, ST_JFLOPS32, ws(WS_NRM), 0, -1, ST_JSWEEPS32,
                pass < 3 ? svd_rec(cur_svd_) : nullptr, svd_stride(), SR_SW0 + pass};
   const int jk = opt_.jacobi_kernel;
   const bool fits2 = m_ub <= 32 * 32 && n_ub <= kJ4MaxN;
+  if (jk == 3 && m_ub > kJrMaxRows)
+    throw Error(TTM_ERR_UNSUPPORTED, "jacobi_kernel = 3 needs Swap matrices of at most 1024 rows");
+  if (jk == 3 || (jk == 0 && m_ub <= kJrMaxRows)) {
+    const int nblk_ub = (n_ub + kJrB - 1) / kJrB;
+    const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
+    JResArgs jr{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, sweeps, h32.counters, h32.tol, h32.delta,
+                h32.fro2, ST_JFLOPS32, ws(WS_NRM), h32.count_nonconv, ST_JSWEEPS32, h32.svd_log, h32.svd_stride,
+                h32.svd_field, 1, -1};
+    timed(1, [&] { jacobi_res<float>(jr, m_ub, nblk_pad_ub); });
+    return;
+  }
   if (jk == 2 && !fits2)
     throw Error(TTM_ERR_UNSUPPORTED, "jacobi_kernel = 2 needs Swap matrices of at most 1024 x 1024");
   if (jk == 8 || jk == 16) {
@@ -505,7 +525,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   TTM_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   if (hs_.ev0 && hs_.ev1) TTM_CUDA(cudaEventElapsedTime(&ms, hs_.ev0, hs_.ev1));
-  double kind_ms[3] = {0.0, 0.0, 0.0};  // GEMMs, float32 Jacobi, Householder QR
+  double kind_ms[4] = {0.0, 0.0, 0.0, 0.0};  // GEMMs, float32 Jacobi, Householder QR, float64 Jacobi
   for (int q = 0; q + 1 < prof_used_; q += 2) {
     float x = 0.f;
     TTM_CUDA(cudaEventElapsedTime(&x, hs_.prof_events[q], hs_.prof_events[q + 1]));
@@ -583,6 +603,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     r.gemm_ms = kind_ms[0];
     r.jacobi32_ms = kind_ms[1];
     r.qr_ms = kind_ms[2];
+    r.jacobi64_ms = kind_ms[3];
     r.jacobi32_flops = stat[(size_t)0 * ns + ST_JFLOPS32];
     r.jacobi32_sweeps = (int64_t)stat[(size_t)z * ns + ST_JSWEEPS32];
     r.gemm_launches = (int64_t)gemm_log_.size();
@@ -664,9 +685,9 @@ static ttm_status check_opts(const ttm_options& o) {
     return set_err(TTM_ERR_UNSUPPORTED, "use_graph and check_finite are not built (must be 0)");
   if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)
     return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
-  if (o.jacobi_kernel != 0 && o.jacobi_kernel != 1 && o.jacobi_kernel != 2 && o.jacobi_kernel != 8 &&
-      o.jacobi_kernel != 16)
-    return set_err(TTM_ERR_INVALID_ARG, "jacobi_kernel must be 0, 1, 2, 8 or 16");
+  if (o.jacobi_kernel != 0 && o.jacobi_kernel != 1 && o.jacobi_kernel != 2 && o.jacobi_kernel != 3 &&
+      o.jacobi_kernel != 8 && o.jacobi_kernel != 16)
+    return set_err(TTM_ERR_INVALID_ARG, "jacobi_kernel must be 0, 1, 2, 3, 8 or 16");
   if (o.newton_steps < 0 || o.newton_steps > kMaxNewtonSteps)
     return set_err(TTM_ERR_INVALID_ARG, "newton_steps must lie in [0, 8]");
   if (o.max_sweeps < 0 || o.max_sweeps > 1000) return set_err(TTM_ERR_INVALID_ARG, "max_sweeps must lie in [0, 1000]");

@@ -21,6 +21,7 @@
 #include "ttm_bjac.cuh"
 #include "ttm_newton.cuh"
 #include "ttm_jac4.cuh"
+#include "ttm_jres.cuh"
 #include "ttm_tc.cuh"
 
 namespace ttm {
@@ -144,7 +145,7 @@ class Engine {
   int ws(int w) const { return nchain_ + w; }
 
   size_t per_product_bytes() const {
-    long e = (long)nchain_ * carriage_elems_ + 3 * t_elems_ + 5 * v_elems_ + 3 * vec_elems_ + vec_elems_ +
+    long e = (long)nchain_ * carriage_elems_ + 3 * t_elems_ + 5 * v_elems_ + 4 * vec_elems_ + vec_elems_ +
              r_elems_ + q_elems_ + (t_elems_ / 2 + 1) + (v_elems_ / 2 + 1) + x_elems_;
     // every buffer aligned to 256 bytes
     return (size_t)e * 8 + (size_t)(nb_ + 1) * 256;
@@ -284,6 +285,30 @@ class Engine {
     void* kargs[] = {args};
     TTM_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(kJ4Warps * 32), kargs, smem, hs_.stream));
     ++launches_;
+  }
+  // Cooperative launch of the resident-block Jacobi: one CTA of kJrB warps per block pair,
+  // as many as fit (one per SM when the columns fill the shared memory).
+  void coop_res(void* fn, void* args, size_t smem, long units) {
+    TTM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    TTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kJrB * 32, smem));
+    if (occ < 1) throw Error(TTM_ERR_UNSUPPORTED, "resident-block Jacobi kernel cannot be made resident");
+    const long blocks = std::max(1L, std::min((long)occ * hs_.num_sms, units));
+    void* kargs[] = {args};
+    TTM_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(kJrB * 32), kargs, smem, hs_.stream));
+    ++launches_;
+  }
+  // The resident-block Jacobi for Swap matrices of at most kJrMaxRows rows, instantiated for
+  // the rows per lane that cover m_ub.
+  template <typename T>
+  void jacobi_res(JResArgs& jr, int m_ub, int nblk_pad_ub) {
+    const int rows = (m_ub + 31) / 32;
+    const int R = rows <= 1 ? 1 : rows <= 2 ? 2 : rows <= 4 ? 4 : rows <= 8 ? 8 : rows <= 16 ? 16 : 32;
+    void* fn = R == 1 ? (void*)jacobi_res_kernel<T, kJrB, 1> : R == 2 ? (void*)jacobi_res_kernel<T, kJrB, 2>
+             : R == 4 ? (void*)jacobi_res_kernel<T, kJrB, 4> : R == 8 ? (void*)jacobi_res_kernel<T, kJrB, 8>
+             : R == 16 ? (void*)jacobi_res_kernel<T, kJrB, 16> : (void*)jacobi_res_kernel<T, kJrB, 32>;
+    const size_t smem = (size_t)2 * kJrB * 32 * R * sizeof(T);
+    coop_res(fn, &jr, smem, (long)Z_ * (nblk_pad_ub / 2));
   }
   // co-resident 256-thread CTAs per SM of the block Jacobi kernels (queried on first use)
   int bjac_occ_[2] = {0, 0};

@@ -19,7 +19,9 @@
 //     cut are dropped together whatever their coupling, and their columns still carry
 //     couplings at float32 level inherited from the float32 passes, which a first-order
 //     step cannot resolve;
-//   - couplings above the float64 noise floor kNewtonFloor sqrt(max(d_i, d_j) trace G);
+//   - couplings above the float64 noise floor kNewtonFloor sqrt(max(d_i, d_j) trace G), the
+//     floor of the float64 Jacobi (a coupling g left below it leaks at most g / |w_big| of a
+//     kept column into a dropped one, so the floor bounds what an exact product loses);
 //   - |S_ij| <= kNewtonMaxS: a pair nearly degenerate relative to its coupling is left
 //     alone (counted as frozen).
 // The steps need the float32 passes to have resolved every relevant pair to float32
@@ -36,7 +38,7 @@ namespace ttm {
 
 constexpr double kNewtonMaxS = 0.25;
 constexpr double kNewtonRelevance = 1e-6;
-constexpr double kNewtonFloor = 1e-13;
+constexpr double kNewtonFloor = 64 * 1.11e-16;
 
 struct NewtonArgs {
   Tables t;
@@ -86,7 +88,8 @@ __global__ void newton_x_kernel(NewtonArgs a) {
           const double dcut = bufp(a.t, z, a.bsort)[max(0, min(kp, n) - 1)];
           const double tr = a.t.stat[z * a.t.ns + a.slot_trace];
           const double num = 0.5 * e * (di + dj) - g, den = di - dj;
-          const bool relevant = dmax >= kNewtonRelevance * dcut && fabs(num) > kNewtonFloor * sqrt(dmax * tr);
+          const bool relevant = dmax >= kNewtonRelevance * dcut &&
+                                fabs(num) > kNewtonFloor * sqrt(dmax * tr);
           if (relevant) {
             if (fabs(num) <= kNewtonMaxS * fabs(den))
               s = num / den;

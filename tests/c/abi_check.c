@@ -78,6 +78,7 @@ int main(void) {
   FIELD(ttm_report, n_frozen_pairs); FIELD(ttm_report, gemm_flops); FIELD(ttm_report, gemm_launches);
   FIELD(ttm_report, qr_ms); FIELD(ttm_report, n_fallback);
   FIELD(ttm_report, jacobi32_sweeps); FIELD(ttm_report, svd_trace); FIELD(ttm_report, svd_trace_len);
+  FIELD(ttm_report, jacobi64_ms);
 #undef FIELD
 
   if (failures == 0) printf("c abi check ok\n");
