@@ -45,7 +45,11 @@ def parse():
     p.add_argument("--chi", type=int, default=512)
     p.add_argument("--L", type=int, default=30)
     p.add_argument("--eps", type=float, default=1e-14)
-    p.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split"])
+    p.add_argument("--prec", default="bf16_split", choices=["fp64", "bf16_split"],
+                   help="bf16_split (the mixed form, default): GEMMs as bf16 digit products on the tensor "
+                        "cores; fp64: GEMMs on the float64 pipe")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the float64 product of the same inputs that the mixed result is compared with")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--f32-passes", type=int, default=0, help="float32 Jacobi passes (0: library default)")
@@ -354,11 +358,20 @@ def kernel_roofline(args, reps, t_local):
                         "ms": gemm_ms, "launches": n_g})
     j_ms = sum(r["jacobi32_ms"] for r in reps)
     j_fl = sum(r["jacobi32_flops"] for r in reps)
-    kernels.append({"bound": "alu", "kernel": "hestenes_kernel<float> (one-sided Jacobi, float32)",
+    jk = getattr(args, "jacobi_kernel", 0)
+    jname = {0: "jacobi_res_kernel<float> (resident-block one-sided Jacobi, float32)",
+             1: "hestenes_kernel<float> (one-sided Jacobi, float32)",
+             2: "jacobi4_kernel (two-column one-sided Jacobi, float32)",
+             3: "jacobi_res_kernel<float> (resident-block one-sided Jacobi, float32)",
+             8: "block_jacobi_kernel<8> (float32)", 16: "block_jacobi_kernel<16> (float32)"}[jk]
+    kernels.append({"bound": "alu", "kernel": jname,
                     "achieved": (j_fl / (j_ms / 1e3) / 1e12) if j_ms > 0 else None, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "peak_source": "nominal float32 rate, 128 FFMA/clk/SM x 152 SMs x 2.07 GHz "
                                                       "(a torch SGEMM probe of this pool reached 69.8)",
                     "ms": j_ms, "launches": sum(r["jacobi_launches"] for r in reps)})
+    kernels.append({"bound": "alu", "kernel": "jacobi_res_kernel<double> (float64 one-sided Jacobi of the "
+                    "Newton fallback)", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "ms": sum(r.get("jacobi64_ms", 0.0) for r in reps), "launches": None})
     kernels.append({"bound": "latency", "kernel": "householder_kernel (float64 QR of the gauge moves)",
                     "achieved": None, "peak": None, "unit": None, "ms": sum(r["qr_ms"] for r in reps),
                     "launches": None})
@@ -372,6 +385,64 @@ def kernel_roofline(args, reps, t_local):
     return roof
 
 
+def tt_norm(cores):
+    """2-norm of a TT (host float64 arrays) by a left-orthogonalising QR sweep: the norm of the
+    last core, without the cancellation of an inner-product sweep."""
+    carry = None
+    for k, c in enumerate(cores):
+        c = c if carry is None else np.tensordot(carry, c, axes=(1, 0))
+        a, d, b = c.shape
+        if k == len(cores) - 1:
+            return float(np.linalg.norm(c))
+        q, carry = np.linalg.qr(c.reshape(a * d, b))
+    return 0.0
+
+
+def stacked_difference(X, Y):
+    """Cores of the TT X - Y with block-stacked bonds (bond D_X + D_Y)."""
+    L = len(X)
+    out = []
+    for k in range(L):
+        x, y = X[k], Y[k]
+        if L == 1:
+            out.append(x - y)
+        elif k == 0:
+            out.append(np.concatenate([x, -y], axis=2))
+        elif k == L - 1:
+            out.append(np.concatenate([x, y], axis=0))
+        else:
+            c = np.zeros((x.shape[0] + y.shape[0], x.shape[1], x.shape[2] + y.shape[2]))
+            c[:x.shape[0], :, :x.shape[2]] = x
+            c[x.shape[0]:, :, x.shape[2]:] = y
+            out.append(c)
+    return out
+
+
+def accuracy_vs_fp64(pkg, h, Ag, Bg, kw, out_mixed, rep_mixed, stream):
+    """One float64 product (GEMMs on the float64 pipe) of the same inputs, timed on its own, and
+    the relative 2-norm difference of the mixed result from it."""
+    import torch
+    kf = dict(kw, prec="fp64")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    of, rf = pkg.ttm_multiply(h, Ag, Bg, **kf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    Om = [c.cpu().numpy() for c in out_mixed]
+    Of = [c.cpu().numpy() for c in of]
+    nf = tt_norm(Of)
+    same = [c.shape for c in Om] == [c.shape for c in Of]
+    diff = tt_norm(stacked_difference(Om, Of)) / nf if same else None
+    return {"rel_err_vs_fp64": diff, "bound": 1e-7,
+            "bonds_equal": same,
+            "discarded_weight_rel_diff": abs(rep_mixed["discarded_weight"] - rf["discarded_weight"])
+            / max(rf["discarded_weight"], 1e-300),
+            "fp64_ms_per_product": e0.elapsed_time(e1), "fp64_status": rf["status"],
+            "what": "||O_mixed - O_fp64||_2 / ||O_fp64||_2 of the last timed product against one float64 product "
+                    "of the same inputs (host QR sweep of the block-stacked difference train)"}
+
+
 def make_line(args, reps, t_local, t, world, e2e, clocks):
     """The bench JSON line (without cpu_baseline) from the reports of the timed steps, one
     report per step (launch-wide figures: a batched step shares its launches).
@@ -382,7 +453,10 @@ def make_line(args, reps, t_local, t, world, e2e, clocks):
     return {
         "metric": METRIC, "value": products / t, "unit": "products/s", "n_gpus": world, "steps": len(reps),
         "warmup": args.warmup, "ms_per_step": 1e3 * t / len(reps), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if getattr(args, "prec", "fp64") == "fp64" else
+                 "mixed: f64 results, GEMMs as bf16 digit products (f32 accumulate), f32+f64 SVD",
+        "data": "synthetic",
         "config": config(args),
         "tflops_counted": flops * products / t / 1e12,
         "roofline": kernel_roofline(args, reps, t_local),
@@ -423,11 +497,17 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    last = {}
+
     def step(profile=0):
         """One step through the public call; returns the step's (launch-wide) report."""
         if args.batch == 1:
-            return pkg.ttm_multiply(h, Ag, Bg, profile=profile, **kw)[1]
-        return pkg.ttm_multiply_batched(h, pairs, profile=profile, **kw)[1][0]
+            out, rep = pkg.ttm_multiply(h, Ag, Bg, profile=profile, **kw)
+            last["out"] = out
+            return rep
+        outs, reps_ = pkg.ttm_multiply_batched(h, pairs, profile=profile, **kw)
+        last["out"] = outs[0]
+        return reps_[0]
 
     for _ in range(args.warmup):
         step()
@@ -445,6 +525,8 @@ def main():
             if q > 0:
                 mean = sum(dts) / len(dts)
                 rest = mean * (1 + args.e2e_steps) + (0.0 if args.no_cpu_baseline else CPU_BASELINE_S + 20.0)
+                if args.prec != "fp64" and not args.no_accuracy:
+                    rest += 1.5 * mean + 10.0     # the float64 product and the host norm
                 proj = max_over_ranks(dist, time.monotonic() - T_START + rest, dev)
                 if proj > args.time_budget:
                     stopped = True
@@ -484,11 +566,21 @@ def main():
     e2e_max = max_over_ranks(dist, e2e_t, dev)
     e2e_val = world * args.e2e_steps * args.batch / e2e_max if e2e_max > 0 else None
 
+    # the mixed result against the float64 product of the same inputs (rank 0, untimed for value)
+    accuracy = None
+    if rank == 0 and args.prec != "fp64" and not args.no_accuracy and "out" in last:
+        try:
+            accuracy = accuracy_vs_fp64(pkg, h, Ag, Bg, kw, last["out"], reps[-1], stream)
+        except Exception as ex:
+            accuracy = {"error": repr(ex)}
+
     if rank == 0:
         line = make_line(args, reps, t_local, t, world,
                          {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d,
                           "d2h_bytes_per_step": d2h, **({"error": e2e_err} if e2e_err else {})},
                          clk.summary())
+        if accuracy is not None:
+            line["accuracy"] = accuracy
         if stopped:
             line["steps_requested"] = args.steps
             line["stopped_early"] = ("the next step would have ended the run after --time-budget %.0f s "

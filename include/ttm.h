@@ -90,8 +90,9 @@ typedef struct {
                                (or chi_max = 0) a final TT-SVD rounding truncates bonds
                                1..L-1 in order with this cap and the eps rule, leaving the
                                norm on the last core (built; not yet run on a GPU)        */
-  int32_t max_sweeps;       /* sweep limit of the float32 Jacobi passes after the first;
-                               0 = 30                                                     */
+  int32_t max_sweeps;       /* sweep limit of the float32 Jacobi passes after the first
+                               and of the float64 Jacobi of the Newton fallback; 0 = 30
+                               and 40                                                     */
   int32_t use_graph;        /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
   int32_t check_finite;     /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
   int32_t profile_kernels;  /* 1: time every GEMM, float32 Jacobi and Householder launch

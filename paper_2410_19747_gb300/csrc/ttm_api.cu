@@ -195,15 +195,15 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
         if (fv != ws(WS_V0)) fr.push_back(fv);
         fv = vn;
       }
-      HestArgs h64{tab_, fw, fv, m, n, npad_ub, kPolishSweeps, counters_ + (size_t)sw64 * counter_stride_, 1e-10,
+      HestArgs h64{tab_, fw, fv, m, n, npad_ub, polish_sweeps(), counters_ + (size_t)sw64 * counter_stride_, 1e-10,
                    64 * 1.11e-16, fro2_ + (size_t)sw64 * Z_, 0, ST_JFLOPS, ws(WS_NRM), 1, IS_FALLBACK, -1, nullptr,
                    0, 0};
       if (m_ub <= kJrMaxRows) {  // the resident-block kernel on all pairs of the fallback products
         const int nblk_ub = (n_ub + kJrB - 1) / kJrB;
         const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
-        JResArgs j64{tab_, fw, fv, m, n, nblk_pad_ub, kPolishSweeps, h64.counters, h64.tol, h64.delta, h64.fro2,
-                     ST_JFLOPS, ws(WS_NRM), 1, -1, nullptr, 0, 0, 0, IS_FALLBACK};
-        timed(3, [&] { jacobi_res<double>(j64, m_ub, nblk_pad_ub); });
+        JResArgs j64{tab_, fw, fv, m, n, nblk_pad_ub, polish_sweeps(), h64.counters, h64.tol, h64.delta, h64.fro2,
+                     ST_JFLOPS, ws(WS_NRM), 1, -1, nullptr, 0, 0, 0, IS_FALLBACK, 0};
+        timed(3, [&] { jacobi_res<double>(j64, m_ub, n_ub, nblk_pad_ub); });
       } else {
         timed(3, [&] { coop((void*)hestenes_kernel<double>, &h64, 1, pairs); });
       }
@@ -246,8 +246,8 @@ void Engine::jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int 
     const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
     JResArgs jr{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, sweeps, h32.counters, h32.tol, h32.delta,
                 h32.fro2, ST_JFLOPS32, ws(WS_NRM), h32.count_nonconv, ST_JSWEEPS32, h32.svd_log, h32.svd_stride,
-                h32.svd_field, 1, -1};
-    timed(1, [&] { jacobi_res<float>(jr, m_ub, nblk_pad_ub); });
+                h32.svd_field, 1, -1, 0};
+    timed(1, [&] { jacobi_res<float>(jr, m_ub, n_ub, nblk_pad_ub); });
     return;
   }
   if (jk == 2 && !fits2)

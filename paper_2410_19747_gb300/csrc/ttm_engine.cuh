@@ -162,6 +162,8 @@ class Engine {
     return b;
   }
   // Sweep counters per product and Jacobi launch: room for the sweep limit of any pass.
+  // sweep limit of the float64 Jacobi of the fallback (max_sweeps when set)
+  int polish_sweeps() const { return opt_.max_sweeps > 0 ? opt_.max_sweeps : kPolishSweeps; }
   int counter_sweeps() const {
     return std::max(std::max(opt_.max_sweeps, kPolishSweeps), std::max(kF32Sweeps, kF32FirstPassSweeps));
   }
@@ -301,14 +303,18 @@ class Engine {
   // The resident-block Jacobi for Swap matrices of at most kJrMaxRows rows, instantiated for
   // the rows per lane that cover m_ub.
   template <typename T>
-  void jacobi_res(JResArgs& jr, int m_ub, int nblk_pad_ub) {
+  void jacobi_res(JResArgs& jr, int m_ub, int n_ub, int nblk_pad_ub) {
     const int rows = (m_ub + 31) / 32;
     const int R = rows <= 1 ? 1 : rows <= 2 ? 2 : rows <= 4 ? 4 : rows <= 8 ? 8 : rows <= 16 ? 16 : 32;
     void* fn = R == 1 ? (void*)jacobi_res_kernel<T, kJrB, 1> : R == 2 ? (void*)jacobi_res_kernel<T, kJrB, 2>
              : R == 4 ? (void*)jacobi_res_kernel<T, kJrB, 4> : R == 8 ? (void*)jacobi_res_kernel<T, kJrB, 8>
              : R == 16 ? (void*)jacobi_res_kernel<T, kJrB, 16> : (void*)jacobi_res_kernel<T, kJrB, 32>;
-    const size_t smem = (size_t)2 * kJrB * 32 * R * sizeof(T);
-    coop_res(fn, &jr, smem, (long)Z_ * (nblk_pad_ub / 2));
+    const size_t smem_w = (size_t)2 * kJrB * 32 * R * sizeof(T);
+    // V's 2B columns join W in shared memory when both fit
+    const int v_rows = (n_ub + 3) / 4 * 4;
+    const size_t smem_v = (size_t)2 * kJrB * v_rows * sizeof(T);
+    jr.v_rows = smem_w + smem_v <= kJrSmemBudget ? v_rows : 0;
+    coop_res(fn, &jr, smem_w + (jr.v_rows ? smem_v : 0), (long)Z_ * (nblk_pad_ub / 2));
   }
   // co-resident 256-thread CTAs per SM of the block Jacobi kernels (queried on first use)
   int bjac_occ_[2] = {0, 0};

@@ -7,6 +7,8 @@ so a field renamed on one side and not the other fails here, not at the end of a
 import json
 import types
 
+import numpy as np
+
 import bench
 from paper_2410_19747_gb300 import binding
 
@@ -50,7 +52,7 @@ def test_contract_keys_and_values():
 def test_roofline_picks_the_dominant_kernel_family():
     roof = line_for([fake_report()], 25.0)["roofline"]
     # float32 Jacobi: 12 s of 25 s; GEMMs 9 s; QR 3 s
-    assert roof["kernel"].startswith("hestenes_kernel<float>")
+    assert roof["kernel"].startswith("jacobi_res_kernel<float>")
     assert roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
     assert abs(roof["achieved"] - 3.0e16 / 12.0 / 1e12) < 1e-9
     assert abs(roof["frac"] - roof["achieved"] / bench.FP32_PEAK_TFLOPS) < 1e-12
@@ -139,3 +141,17 @@ def test_schedule_flops_match_the_oracles_realised_schedule():
         ott.left_canonical = lc
     got = bench.schedule_flops([1] + [c.shape[2] for c in A], [1] + [c.shape[2] for c in B], d, cap)
     assert abs(got - (tot[0] + prep[0])) <= 1e-9 * got
+
+
+def test_accuracy_helpers_against_dense():
+    """The bench's difference norm (QR sweep of the block-stacked difference) equals the dense
+    2-norm of X - Y."""
+    import ttgen
+    from oracle import tt as ott
+    X = ttgen.rand_tt(9, 2, 6, 81)
+    Y = ttgen.rand_tt(9, 2, 5, 82)
+    dx, dy = ott.dense(X), ott.dense(Y)
+    assert abs(bench.tt_norm(X) - np.linalg.norm(dx)) <= 1e-12 * np.linalg.norm(dx)
+    dd = np.linalg.norm(dx - dy)
+    assert abs(bench.tt_norm(bench.stacked_difference(X, Y)) - dd) <= 1e-12 * dd
+    assert bench.tt_norm(bench.stacked_difference(X, X)) <= 1e-13 * np.linalg.norm(dx)
