@@ -109,7 +109,8 @@ typedef struct {
                                16 = Gram-based block Jacobi on blocks of that many
                                columns                                                   */
   int32_t newton_steps;     /* float64 Newton steps that finish every Swap SVD after the
-                               float32 passes: 0 = 3, 1..8 accepted                      */
+                               float32 passes: 0 = 3, 1..8 accepted; an SVD whose last
+                               correction is still above 1e-7 takes up to 2 more          */
   int32_t split_digits;     /* digits per operand of TTM_PREC_BF16_SPLIT: 0 = 8, 2..8   */
   int32_t reserved1;        /* must be 0                                                 */
   int64_t env_budget_bytes; /* ttm_backward: device memory for the stored left
@@ -146,8 +147,9 @@ typedef struct {
   int64_t n_nonconverged;      /* SVDs that did not converge (see TTM_WARN_NOT_CONVERGED) */
   int64_t n_frozen_pairs;      /* column pairs the last Newton steps left unrotated as
                                   degenerate relative to their coupling                    */
-  double gemm_flops;           /* algorithmic flops of those GEMMs from the realised bonds
-                                  (2 M N K; M (M + 1) K for a symmetric Gram), launch-wide */
+  double gemm_flops;           /* algorithmic flops of the GEMM problems executed (2 M N K;
+                                  M (M + 1) K for a symmetric Gram), counted on the device,
+                                  launch-wide; problems a predicate left empty count 0      */
   int64_t gemm_launches;       /* GEMMs of the call (launch-wide)                          */
   double qr_ms;                /* device time of the Householder QR launches
                                   (profile_kernels = 1), else 0                            */

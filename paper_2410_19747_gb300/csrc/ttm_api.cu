@@ -172,6 +172,30 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
       fr.push_back(xb);
       vb = mm;
     }
+    // up to kNewtonExtraSteps more steps for the products whose last correction is still above
+    // float64 level (the quadratic convergence from a correction near 0.1 needs five steps);
+    // every launch is empty for the others, which keep their W and V
+    for (int e = 0; e < kNewtonExtraSteps; ++e) {
+      launch_small(newton_more_kernel, cdiv(Z_, 128), 128);
+      const int g = take(), mm = take(), xb = take();
+      gemm(PredFn<GramFn>{GramFn{tab_, wb, g, m, n}, IS_NEWTON_MORE, 1, tab_}, 1, n_ub, n_ub, m_ub,
+           GemmShape{n, n, m, 1, 1});
+      gemm(PredFn<GramFn>{GramFn{tab_, vb, mm, n, n}, IS_NEWTON_MORE, 1, tab_}, 1, n_ub, n_ub, n_ub,
+           GemmShape{n, n, n, 1, 1});
+      newton_x(g, mm, xb, n, n_ub, nprov, 0, true, IS_NEWTON_MORE);
+      if (tc_) colexp(wb, m, n, n_ub);
+      gemm(PredFn<ThetaVFn>{ThetaVFn{tab_, wb, xb, wo, m, n}, IS_NEWTON_MORE, 1, tab_}, 1, m_ub, n_ub, n_ub,
+           GemmShape{m, n, n, 1, 0}, tc_ ? ws(WS_TAU) : -1);  // W <- W X
+      pcopy(wb, wo, m, n, IS_NEWTON_MORE, 0, (long)m_ub * n_ub);
+      std::swap(wb, wo);
+      gemm(PredFn<ThetaVFn>{ThetaVFn{tab_, vb, xb, mm, n, n}, IS_NEWTON_MORE, 1, tab_}, 1, n_ub, n_ub, n_ub,
+           GemmShape{n, n, n, 1, 0});  // V <- V X
+      pcopy(vb, mm, n, n, IS_NEWTON_MORE, 0, (long)n_ub * n_ub);
+      fr.push_back(vb);
+      fr.push_back(g);
+      fr.push_back(xb);
+      vb = mm;
+    }
     launch_small(newton_check_kernel, cdiv(Z_, 128), 128);
     // 3b. fallback for the products whose Newton residual stayed above float64 level (every
     //     launch below is empty for the others): restart from the state after the float32
@@ -202,7 +226,7 @@ int Engine::swap(int x, int y, int bl, int bm, int br, int kind) {
         const int nblk_ub = (n_ub + kJrB - 1) / kJrB;
         const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
         JResArgs j64{tab_, fw, fv, m, n, nblk_pad_ub, polish_sweeps(), h64.counters, h64.tol, h64.delta, h64.fro2,
-                     ST_JFLOPS, ws(WS_NRM), 1, -1, nullptr, 0, 0, 0, IS_FALLBACK, 0};
+                     ST_JFLOPS, ws(WS_NRM), 1, -1, nullptr, 0, 0, 0, IS_FALLBACK};
         timed(3, [&] { jacobi_res<double>(j64, m_ub, n_ub, nblk_pad_ub); });
       } else {
         timed(3, [&] { coop((void*)hestenes_kernel<double>, &h64, 1, pairs); });
@@ -246,7 +270,7 @@ void Engine::jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int 
     const int nblk_pad_ub = nblk_ub + (nblk_ub & 1);
     JResArgs jr{tab_, ws(WS_W32), ws(WS_V32), m, n, nblk_pad_ub, sweeps, h32.counters, h32.tol, h32.delta,
                 h32.fro2, ST_JFLOPS32, ws(WS_NRM), h32.count_nonconv, ST_JSWEEPS32, h32.svd_log, h32.svd_stride,
-                h32.svd_field, 1, -1, 0};
+                h32.svd_field, 1, -1};
     timed(1, [&] { jacobi_res<float>(jr, m_ub, n_ub, nblk_pad_ub); });
     return;
   }
@@ -607,13 +631,8 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     r.jacobi32_flops = stat[(size_t)0 * ns + ST_JFLOPS32];
     r.jacobi32_sweeps = (int64_t)stat[(size_t)z * ns + ST_JSWEEPS32];
     r.gemm_launches = (int64_t)gemm_log_.size();
-    double gf = 0.0;
-    for (const GemmShape& gs : gemm_log_)
-      for (int zz = 0; zz < Z_; ++zz) {  // launch-wide, like the other kernel figures
-        auto dv = [&](const Dim& dd) { return dd.id < 0 ? (double)dd.mul : (double)dd.mul * bonds[(size_t)zz * nbd + dd.id]; };
-        const double M = dv(gs.M), N = dv(gs.N), K = dv(gs.K);
-        gf += gs.nbatch * (gs.sym ? M * (N + 1) * K : 2.0 * M * N * K);
-      }
+    double gf = 0.0;  // counted on the device per executed problem; launch-wide like the others
+    for (int zz = 0; zz < Z_; ++zz) gf += stat[(size_t)zz * ns + ST_GFLOPS];
     r.gemm_flops = gf;
     if (user_svd && svd_cap > 0) {
       const int64_t nrec = std::min<int64_t>(svd_cap, n_trunc_);

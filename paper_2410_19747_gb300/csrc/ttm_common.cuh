@@ -37,10 +37,10 @@ __device__ __forceinline__ double* bufp(const Tables& t, int z, int id) {
 
 // istat slots
 enum { IS_STATUS = 0, IS_MAX_BOND = 1, IS_SWEEPS_MAX = 2, IS_NONCONV = 3, IS_NFROZEN = 4, IS_NEWTON_BAD = 5,
-       IS_ROUND = 6, IS_CAST_EXP = 7, IS_FALLBACK = 8, IS_NFIXED = 9 };
+       IS_ROUND = 6, IS_CAST_EXP = 7, IS_FALLBACK = 8, IS_NEWTON_MORE = 9, IS_NFIXED = 10 };
 // stat slots (the per-truncation weights follow from ST_NFIXED)
 enum { ST_WSUM = 0, ST_WSQRT = 1, ST_NEWTON_RES = 2, ST_JFLOPS32 = 3, ST_NEWTON_CUR = 4, ST_TRACE = 5,
-       ST_JFLOPS = 6, ST_JSWEEPS32 = 7, ST_NFIXED = 8 };
+       ST_JFLOPS = 6, ST_JSWEEPS32 = 7, ST_GFLOPS = 8, ST_NFIXED = 9 };
 
 // Per-SVD diagnostic record (the report's svd_trace): m, n, k, float32 sweeps of passes
 // 0, 1, 2, fallback flag.

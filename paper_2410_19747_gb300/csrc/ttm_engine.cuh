@@ -198,13 +198,14 @@ class Engine {
     timed(0, [&] {
       if (tc_) {
         const cudaError_t e = launch_tc_gemm(hs_.stream, f, Z_, nbatch, M_ub, N_ub, K_ub, kscale_buf,
-                                             split_digits(), d_tc_, d_istat_ + IS_STATUS);
+                                             split_digits(), d_tc_, d_istat_ + IS_STATUS, d_stat_ + ST_GFLOPS,
+                                             tab_.ns);
         if (e != cudaSuccess)
           throw Error(TTM_ERR_CUDA, std::string("tensor-core GEMM, ") + tc_failed_step() + ": " + cudaGetErrorString(e));
         launches_ += 6;
       } else {
         dim3 grid(cdiv(N_ub, GT), cdiv(M_ub, GT), (unsigned)(Z_ * nbatch));
-        dgemm_kernel<F><<<grid, 256, 0, hs_.stream>>>(f, nbatch);
+        dgemm_kernel<F><<<grid, 256, 0, hs_.stream>>>(f, nbatch, d_stat_ + ST_GFLOPS, tab_.ns);
         TTM_CUDA(cudaGetLastError());
         ++launches_;
       }
@@ -309,12 +310,9 @@ class Engine {
     void* fn = R == 1 ? (void*)jacobi_res_kernel<T, kJrB, 1> : R == 2 ? (void*)jacobi_res_kernel<T, kJrB, 2>
              : R == 4 ? (void*)jacobi_res_kernel<T, kJrB, 4> : R == 8 ? (void*)jacobi_res_kernel<T, kJrB, 8>
              : R == 16 ? (void*)jacobi_res_kernel<T, kJrB, 16> : (void*)jacobi_res_kernel<T, kJrB, 32>;
-    const size_t smem_w = (size_t)2 * kJrB * 32 * R * sizeof(T);
-    // V's 2B columns join W in shared memory when both fit
-    const int v_rows = (n_ub + 3) / 4 * 4;
-    const size_t smem_v = (size_t)2 * kJrB * v_rows * sizeof(T);
-    jr.v_rows = smem_w + smem_v <= kJrSmemBudget ? v_rows : 0;
-    coop_res(fn, &jr, smem_w + (jr.v_rows ? smem_v : 0), (long)Z_ * (nblk_pad_ub / 2));
+    (void)n_ub;
+    const size_t smem = (size_t)2 * kJrB * 32 * R * sizeof(T);
+    coop_res(fn, &jr, smem, (long)Z_ * (nblk_pad_ub / 2));
   }
   // co-resident 256-thread CTAs per SM of the block Jacobi kernels (queried on first use)
   int bjac_occ_[2] = {0, 0};

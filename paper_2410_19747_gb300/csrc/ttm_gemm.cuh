@@ -33,6 +33,15 @@ struct GemmDesc {
 
 constexpr int GT = 64, GK = 16;
 
+// Realised flops of one problem (2 M N K; M (M + 1) K for a symmetric Gram whose upper
+// triangle is formed), added by one thread of the problem's first tile when fl is set: a
+// predicated-off problem (M = 0) adds nothing.
+__device__ __forceinline__ void gemm_count_flops(double* fl, int fl_stride, int z, const GemmDesc& g) {
+  if (fl == nullptr) return;
+  const double f = g.upper ? (double)g.M * (g.N + 1) * g.K : 2.0 * g.M * g.N * g.K;
+  atomicAdd(fl + (long)z * fl_stride, f);
+}
+
 // Realised shape of a launch's GEMMs (per product and batch index), for the flop count.
 struct GemmShape {
   Dim M, N, K;
@@ -41,11 +50,12 @@ struct GemmShape {
 };
 
 template <class F>
-__global__ void __launch_bounds__(256) dgemm_kernel(F f, int nbatch) {
+__global__ void __launch_bounds__(256) dgemm_kernel(F f, int nbatch, double* fl = nullptr, int fl_stride = 0) {
   const int z = blockIdx.z / nbatch, bi = blockIdx.z % nbatch;
   const GemmDesc g = f(z, bi);
   const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
   if (g.M <= 0 || g.N <= 0 || m0 >= g.M || n0 >= g.N) return;
+  if (m0 == 0 && n0 == 0 && threadIdx.x == 0) gemm_count_flops(fl, fl_stride, z, g);
   if (g.upper && m0 > n0) return;
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];

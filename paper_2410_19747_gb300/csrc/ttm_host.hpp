@@ -31,6 +31,7 @@ constexpr int kDefaultF32Passes = 3;   // float32 Jacobi passes of every Swap SV
 constexpr int kMaxF32Passes = 8;
 constexpr int kF32Sweeps = 30;         // sweep limit of the later float32 passes
 constexpr int kDefaultNewtonSteps = 3; // float64 Newton steps after the float32 passes
+constexpr int kNewtonExtraSteps = 2;   // further steps for an SVD whose last correction is above 1e-7
 constexpr int kMaxNewtonSteps = 8;
 constexpr int kPolishSweeps = 40;      // sweep limit of the float64 Jacobi of the fallback
 // Sweep limit of the first float32 pass: it only has to grade W (the next pass redoes the

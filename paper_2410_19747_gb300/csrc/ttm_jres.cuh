@@ -28,7 +28,6 @@ namespace ttm {
 
 constexpr int kJrB = 8;         // columns per block; one warp per pair of an inner round
 constexpr int kJrMaxRows = 1024;  // rows held per column (32 lanes x 32)
-constexpr size_t kJrSmemBudget = 200 * 1024;  // dynamic shared memory for W and the staged V
 
 struct JResArgs {
   Tables t;
@@ -48,8 +47,6 @@ struct JResArgs {
   int svd_stride, svd_field;
   int init_v;        // 1: V starts at I; 0: V holds a starting rotation
   int islot_pred;    // -1, or istat slot: only products whose slot is non-zero take part
-  int v_rows;        // 0: V is read from global memory at the update; else the rows (>= n,
-                     // a multiple of 4) of the 2B V columns staged in shared memory by cp.async
 };
 
 // Pair `i` of round `r` of the round-robin tournament on `k` (even) players.
@@ -139,22 +136,6 @@ __device__ __forceinline__ bool jr_rot<float>(float a, float b, float g, float& 
   s = c * t;
   return true;
 }
-
-// Asynchronous global -> shared copies (cp.async, completion by wait_group; no spin).
-__device__ __forceinline__ void jr_cp16(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-template <int BYTES>
-__device__ __forceinline__ void jr_cp_elem(void* dst, const void* src) {  // one 4- or 8-byte element
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (BYTES == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void jr_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void jr_cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Shared state of one CTA for the block pair it holds. Rows of Q are padded to a multiple
 // of 16 bytes (vector reads in the V update) that spreads the per-lane column updates over
@@ -381,30 +362,6 @@ __global__ void __launch_bounds__(B * 32, 1) jacobi_res_kernel(JResArgs a) {
             for (int u = 0; u < BATCH; ++u) jr_cols[threadIdx.x + (b0 + u) * NT] = v[u];
           }
         }
-        // the 2B columns of V, copied asynchronously while the inner rounds run
-        const bool vstage = a.v_rows > 0;
-        T* jr_v = jr_cols + 2 * B * MR;  // [2B][v_rows]
-        if (vstage) {
-          if ((n % W16) == 0) {
-            const int n4 = n / W16;
-#pragma unroll
-            for (int c = 0; c < 2 * B; ++c) {
-              const int g = S.col[c];
-              if (g < 0) continue;
-              for (int r4 = threadIdx.x; r4 < n4; r4 += NT)
-                jr_cp16(jr_v + (long)c * a.v_rows + r4 * W16, Vm + (long)g * n + r4 * W16);
-            }
-          } else {
-#pragma unroll
-            for (int c = 0; c < 2 * B; ++c) {
-              const int g = S.col[c];
-              if (g < 0) continue;
-              for (int row = threadIdx.x; row < n; row += NT)
-                jr_cp_elem<(int)sizeof(T)>(jr_v + (long)c * a.v_rows + row, Vm + (long)g * n + row);
-            }
-          }
-          jr_cp_commit();
-        }
         __syncthreads();
         T x[R], y[R];
         // pairs inside each block, once per sweep
@@ -444,7 +401,6 @@ __global__ void __launch_bounds__(B * 32, 1) jacobi_res_kernel(JResArgs a) {
           }
           if (px) jr_store<T, R>(cp, lane, x);
         }
-        if (vstage) jr_cp_wait_all();  // this thread's copies of V
         __syncthreads();
         // write back the rotated columns, the marks and V <- V Q
         if (S.nrot > 0) {
@@ -465,18 +421,10 @@ __global__ void __launch_bounds__(B * 32, 1) jacobi_res_kernel(JResArgs a) {
           for (int row0 = threadIdx.x; row0 < n; row0 += 2 * NT) {
             const int row1 = row0 + NT;
             T v0[2 * B], v1[2 * B], o0[2 * B], o1[2 * B];
-            if (vstage) {
 #pragma unroll
-              for (int c = 0; c < 2 * B; ++c) {
-                v0[c] = S.col[c] >= 0 ? jr_v[(long)c * a.v_rows + row0] : T(0);
-                v1[c] = (S.col[c] >= 0 && row1 < n) ? jr_v[(long)c * a.v_rows + row1] : T(0);
-              }
-            } else {
-#pragma unroll
-              for (int c = 0; c < 2 * B; ++c) {
-                v0[c] = S.col[c] >= 0 ? __ldcg(Vm + (long)S.col[c] * n + row0) : T(0);
-                v1[c] = (S.col[c] >= 0 && row1 < n) ? __ldcg(Vm + (long)S.col[c] * n + row1) : T(0);
-              }
+            for (int c = 0; c < 2 * B; ++c) {
+              v0[c] = S.col[c] >= 0 ? __ldcg(Vm + (long)S.col[c] * n + row0) : T(0);
+              v1[c] = (S.col[c] >= 0 && row1 < n) ? __ldcg(Vm + (long)S.col[c] * n + row1) : T(0);
             }
 #pragma unroll
             for (int c = 0; c < 2 * B; ++c) {

@@ -129,6 +129,18 @@ __global__ void newton_x_kernel(NewtonArgs a) {
   }
 }
 
+// Before an extra Newton step: IS_NEWTON_MORE = 1 for a product whose last correction is still
+// above kNewtonConverged (its ST_NEWTON_CUR is reset to record the extra step); the others keep
+// their residual and skip the step.
+__global__ void newton_more_kernel(Tables t) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= t.nz) return;
+  double* st = t.stat + z * t.ns;
+  const bool more = !(st[ST_NEWTON_CUR] <= kNewtonConverged);
+  t.istat[z * t.nis + IS_NEWTON_MORE] = more ? 1 : 0;
+  if (more) st[ST_NEWTON_CUR] = 0.0;
+}
+
 // After the last Newton step: IS_FALLBACK = 1 for a product whose residual stayed above
 // kNewtonConverged (it is counted in IS_NEWTON_BAD and its Swap finishes on the fallback
 // path), the largest residual of the product is kept in ST_NEWTON_RES, and ST_NEWTON_CUR is

@@ -108,6 +108,8 @@ struct OzArgs {
   F f;
   int nbatch;
   OzWs w;
+  double* fl;     // nullptr, or per-product flop accumulators (stride fl_stride)
+  int fl_stride;
 };
 
 // Exponents: e_r = the binary exponent of max_k |X_rk 2^(-+q_k)| (frexp convention, so the
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzArgs<F> a, int
   const GemmDesc g = a.f(z, b);
   const int m0 = blockIdx.y * kOzTM, n0 = blockIdx.x * kOzTN;
   if (g.M <= 0 || g.N <= 0 || m0 >= g.M || n0 >= g.N) return;   // CTA-uniform exit
+  if (m0 == 0 && n0 == 0 && threadIdx.x == 0) gemm_count_flops(a.fl, a.fl_stride, z, g);
   if (g.upper && m0 > n0 + kOzTN - 1) return;
   const int S = a.w.S;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -472,7 +475,7 @@ inline size_t tc_ws_bytes(long nprob, int M_ub, int N_ub, int K_ub, int S) {
 // ws: tc_ws_bytes(nz * nbatch, ...) bytes of device memory; err: int set on a timeout.
 template <class F>
 cudaError_t launch_tc_gemm(cudaStream_t st, const F& f, int nz, int nbatch, int M_ub, int N_ub, int K_ub, int kscale_buf,
-                    int S, unsigned char* ws, int* err) {
+                    int S, unsigned char* ws, int* err, double* fl = nullptr, int fl_stride = 0) {
   const long mpad = oz_cdiv(M_ub, kOzTM) * kOzTM, npad = oz_cdiv(N_ub, kOzTN) * kOzTN;
   const long kpad = oz_cdiv(K_ub > 0 ? K_ub : 1, kOzKC) * kOzKC;
   const long nprob = (long)nz * nbatch;
@@ -489,7 +492,7 @@ cudaError_t launch_tc_gemm(cudaStream_t st, const F& f, int nz, int nbatch, int 
   w.S = S;
   w.err = err;
   w.kscale_buf = kscale_buf;
-  OzArgs<F> oa{f, nbatch, w};
+  OzArgs<F> oa{f, nbatch, w, fl, fl_stride};
   const long ne = 2 * nprob * e_ints;
   // every launch is checked at once: the caller gets the first failing step
   const char*& step = tc_failed_step();
