@@ -86,10 +86,13 @@ typedef struct {
   double eps;               /* Eq. eps threshold on the relative discarded weight of every
                                Swap SVD; 0 keeps every singular value                     */
   int64_t chi_max;          /* cap on the bond of every Swap SVD; 0 = unbounded          */
-  int64_t chi_out;          /* cap on the output bonds; 0 = none. When chi_out < chi_max
-                               (or chi_max = 0) a final TT-SVD rounding truncates bonds
-                               1..L-1 in order with this cap and the eps rule, leaving the
-                               norm on the last core (built; not yet run on a GPU)        */
+  int64_t chi_out;          /* cap on the output bonds; 0 = none. A product with an
+                               output bond above chi_out gets a final TT-SVD rounding that
+                               truncates bonds 1..L-1 in order with this cap and the eps
+                               rule, leaving the norm on the last core; for a product whose
+                               bonds are all within the cap the same sweep keeps every bond
+                               (an exact refactorisation; decided per product on the
+                               device)                                                    */
   int32_t max_sweeps;       /* sweep limit of the float32 Jacobi passes after the first
                                and of the float64 Jacobi of the Newton fallback; 0 = 30
                                and 40                                                     */
