@@ -33,6 +33,13 @@ METRIC = "TTM products/s + TFLOP/s at chi=512,d=2,L=30; mixed vs FP64 at rel err
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz = 1.259
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12  # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz = 80.5
 L2_BYTES = 129 * 2 ** 20
+# DRAM bytes (read + write) per launch of a kernel, from the committed ncu captures (one launch
+# each, named in the source); they describe the kernels as they are at the time of the capture.
+MEASURED_TRAFFIC = {
+    "jacobi_res_kernel<float>": (5.58e6, "profiles/jacobi_res_f32_chi512_L20.md: one full-size float32 pass "
+                                         "(1024 x 1024, 70 ms); W and V stay in L2"),
+    "oz_gemm_kernel": (7.29e6, "profiles/oz_gemm_gram_chi512_L20.md: one 1024^3 Gram"),
+}
 CPU_BASELINE_S = 40.0   # allowance for the CPU baseline leg in the --time-budget projection
 
 
@@ -379,6 +386,10 @@ def kernel_roofline(args, reps, t_local):
         k["frac"] = (k["achieved"] / k["peak"]) if (k["achieved"] and k["peak"]) else None
         k["share_of_step"] = k["ms"] / 1e3 / t_local if t_local > 0 else None
         k["traffic"] = None
+        for prefix, (nbytes, src) in MEASURED_TRAFFIC.items():
+            if k["kernel"].startswith(prefix):
+                k["traffic"] = nbytes
+                k["traffic_source"] = src
     kernels.sort(key=lambda k: -(k["share_of_step"] or 0.0))
     roof = dict(kernels[0])
     roof["other_kernels"] = kernels[1:]
