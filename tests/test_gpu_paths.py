@@ -236,8 +236,11 @@ def test_config3_against_the_oracle(h, chi):
     no2 = ott.inner(Oo, Oo)
     assert abs(rep["norm_out"] ** 2 - no2) <= 1e-9 * no2
     eta = np.sqrt(abs(excess_sq(h, O, Oo, A, B)) / no2)
-    print("chi %d: eta %.3e, distance to the oracle %.3e" % (chi, eta, ott.diff_norm(O, Oo) / np.sqrt(no2)))
-    assert eta <= 1e-5
+    dist = ott.diff_norm(O, Oo) / np.sqrt(no2)
+    print("chi %d: eta %.3e, distance to the oracle %.3e" % (chi, eta, dist))
+    # measured on GB300: distance 2.5e-11 / 3.5e-11 and eta 5.0e-8 / 3.8e-8 at chi = 256 / 512
+    assert dist <= 1e-8
+    assert eta <= 1e-6
 
 
 @pytest.mark.parametrize("chi", [128, 256])
