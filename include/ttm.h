@@ -94,7 +94,7 @@ typedef struct {
                                (an exact refactorisation; decided per product on the
                                device)                                                    */
   int32_t max_sweeps;       /* sweep limit of the float32 Jacobi passes after the first
-                               and of the float64 Jacobi of the Newton fallback; 0 = 30
+                               and of the float64 Jacobi of the Newton fallback; 0 = 20
                                and 40                                                     */
   int32_t use_graph;        /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
   int32_t check_finite;     /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */

@@ -29,7 +29,9 @@ struct Error : std::runtime_error {
 constexpr int kMaxBond = 8192;         // largest bond the planner accepts
 constexpr int kDefaultF32Passes = 3;   // float32 Jacobi passes of every Swap SVD
 constexpr int kMaxF32Passes = 8;
-constexpr int kF32Sweeps = 30;         // sweep limit of the later float32 passes
+constexpr int kF32Sweeps = 20;         // sweep limit of the later float32 passes (the Newton steps
+                                        // finish what they leave; 20 instead of 30 measured 6 % faster
+                                        // at chi = 512 with the same fallbacks and result)
 constexpr int kDefaultNewtonSteps = 3; // float64 Newton steps after the float32 passes
 constexpr int kNewtonExtraSteps = 2;   // further steps for an SVD whose last correction is above 1e-7
 constexpr int kMaxNewtonSteps = 8;
