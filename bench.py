@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--prec", default="bf16_split", choices=["fp64", "bf16_split"],
                    help="bf16_split (the mixed form, default): GEMMs as bf16 digit products on the tensor "
                         "cores; fp64: GEMMs on the float64 pipe")
+    p.add_argument("--no-config1", action="store_true",
+                   help="skip the small-bond side measurement (config 1: L=10, d=2, chi=8, float64)")
     p.add_argument("--no-accuracy", action="store_true",
                    help="skip the float64 product of the same inputs that the mixed result is compared with")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -454,6 +456,35 @@ def accuracy_vs_fp64(pkg, h, Ag, Bg, kw, out_mixed, rep_mixed, stream):
                     "of the same inputs (host QR sweep of the block-stacked difference train)"}
 
 
+def config1_throughput(pkg, h, dev, stream, warmup=5, steps=50):
+    """Small-bond side measurement: products/s of config 1 (L = 10, d = 2, chi_A = chi_B =
+    chi_out = 8, Gaussian cores left-canonicalised, float64 mode, eps = 0), inputs resident,
+    CUDA events around `steps` back-to-back products after `warmup` untimed ones."""
+    import torch
+    import ttgen
+    A = ttgen.rand_tt(10, 2, 8, 1000, canon="left")
+    B = ttgen.rand_tt(10, 2, 8, 1100, canon="left")
+    Ag = [torch.from_numpy(c).to(dev) for c in A]
+    Bg = [torch.from_numpy(c).to(dev) for c in B]
+    kw = dict(eps=0.0, chi_max=8, chi_out=8, prec="fp64")
+    for _ in range(warmup):
+        pkg.ttm_multiply(h, Ag, Bg, **kw)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        _, rep = pkg.ttm_multiply(h, Ag, Bg, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "config1: Gaussian TT pair, L=10, d=2, chi=8, left-canonicalised; float64, eps=0, "
+                        "chi_max=chi_out=8", "products_per_s": 1e3 / ms, "ms_per_product": ms,
+            "kernel_launches_per_product": rep["n_kernel_launches"], "steps": steps, "warmup": warmup,
+            "note": "each call plans, allocates its arena and copies its report back; the time includes that host "
+                    "work between the CUDA events"}
+
+
 def make_line(args, reps, t_local, t, world, e2e, clocks):
     """The bench JSON line (without cpu_baseline) from the reports of the timed steps, one
     report per step (launch-wide figures: a batched step shares its launches).
@@ -585,6 +616,13 @@ def main():
         except Exception as ex:
             accuracy = {"error": repr(ex)}
 
+    small = None
+    if rank == 0 and not args.no_config1:
+        try:
+            small = config1_throughput(pkg, h, dev, stream)
+        except Exception as ex:
+            small = {"error": repr(ex)}
+
     if rank == 0:
         line = make_line(args, reps, t_local, t, world,
                          {"value": e2e_val, "unit": "products/s", "h2d_bytes_per_step": h2d,
@@ -592,6 +630,8 @@ def main():
                          clk.summary())
         if accuracy is not None:
             line["accuracy"] = accuracy
+        if small is not None:
+            line["config1"] = small
         if stopped:
             line["steps_requested"] = args.steps
             line["stopped_early"] = ("the next step would have ended the run after --time-budget %.0f s "

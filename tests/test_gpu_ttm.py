@@ -165,3 +165,22 @@ def test_batched_uneven_chi_equals_single(h):
         assert ott.diff_norm(Oh, O1) <= 1e-12 * ott.norm(O1)
         P = ott.dense(A) * ott.dense(B)
         assert np.linalg.norm(ott.dense(Oh) - P) <= r["err_bound"] * (1 + 1e-9) + 1e-12 * np.linalg.norm(P)
+
+
+def test_batched_config4_shape(h):
+    """A scaled-down config-4 batch: 8 random left-canonical pairs, L = 12, d = 2, bonds drawn
+    from U{16..64}, multiplied in one ttm_multiply_batched call with chi_max = 48 in the mixed
+    mode; every product equals its single call and stays within its error bound of the dense
+    product."""
+    import paper_2410_19747_gb300 as pkg
+    pairs = ttgen.pair_batch(8, 12, 2, 16, 64, 4100)
+    res, reps = pkg.ttm_multiply_batched(h, [(dev(A), dev(B)) for A, B in pairs], chi_max=48, eps=1e-14,
+                                         prec="bf16_split")
+    torch.cuda.synchronize()
+    for (A, B), O, r in zip(pairs, res, reps):
+        O1, r1 = run(h, A, B, chi_max=48, eps=1e-14, prec="bf16_split")
+        Oh = host(O)
+        assert ott.bonds_of(Oh) == ott.bonds_of(O1)
+        assert ott.diff_norm(Oh, O1) <= 1e-9 * ott.norm(O1)
+        P = ott.dense(A) * ott.dense(B)
+        assert np.linalg.norm(ott.dense(Oh) - P) <= r["err_bound"] * (1 + 1e-9) + 1e-12 * np.linalg.norm(P)
