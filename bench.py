@@ -478,11 +478,25 @@ def config1_throughput(pkg, h, dev, stream, warmup=5, steps=50):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    return {"workload": "config1: Gaussian TT pair, L=10, d=2, chi=8, left-canonicalised; float64, eps=0, "
-                        "chi_max=chi_out=8", "products_per_s": 1e3 / ms, "ms_per_product": ms,
-            "kernel_launches_per_product": rep["n_kernel_launches"], "steps": steps, "warmup": warmup,
-            "note": "each call plans, allocates its arena and copies its report back; the time includes that host "
-                    "work between the CUDA events"}
+    out = {"workload": "config1: Gaussian TT pair, L=10, d=2, chi=8, left-canonicalised; float64, eps=0, "
+                       "chi_max=chi_out=8", "products_per_s": 1e3 / ms, "ms_per_product": ms,
+           "kernel_launches_per_product": rep["n_kernel_launches"], "steps": steps, "warmup": warmup,
+           "note": "each call plans, allocates its arena and copies its report back; the time includes that host "
+                   "work between the CUDA events"}
+    try:  # the same with use_graph = 1: the first call captures the plan, the others replay it
+        for _ in range(warmup):
+            pkg.ttm_multiply(h, Ag, Bg, use_graph=1, **kw)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            pkg.ttm_multiply(h, Ag, Bg, use_graph=1, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msg = e0.elapsed_time(e1) / steps
+        out["graph"] = {"products_per_s": 1e3 / msg, "ms_per_product": msg}
+    except Exception as ex:
+        out["graph"] = {"error": repr(ex)}
+    return out
 
 
 def make_line(args, reps, t_local, t, world, e2e, clocks):

@@ -96,7 +96,11 @@ typedef struct {
   int32_t max_sweeps;       /* sweep limit of the float32 Jacobi passes after the first
                                and of the float64 Jacobi of the Newton fallback; 0 = 20
                                and 40                                                     */
-  int32_t use_graph;        /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
+  int32_t use_graph;        /* 1: ttm_multiply / ttm_multiply_batched capture the kernel
+                               sequence of a plan (options, shapes, input bonds, arena) into
+                               a CUDA graph on first use and replay it while the plan stays
+                               the same (input copies are issued before each replay); not
+                               with profile_kernels = 1. 0: launch every kernel directly  */
   int32_t check_finite;     /* must be 0 (1 returns TTM_ERR_UNSUPPORTED)                  */
   int32_t profile_kernels;  /* 1: time every GEMM, float32 Jacobi and Householder launch
                                with CUDA events on the handle's stream (fills gemm_ms,

@@ -233,12 +233,12 @@ def _shape_out(o, bufs, d):
 
 
 def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                         f32_passes=0, jacobi_kernel=0, newton_steps=0, split_digits=0):
+                         f32_passes=0, jacobi_kernel=0, newton_steps=0, split_digits=0, use_graph=0):
     """[(A_i, B_i)] -> ([Omega_i], [report_i]) with one batched launch sequence (ttm_multiply_batched)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
                        profile=profile, f32_passes=f32_passes, jacobi_kernel=jacobi_kernel,
-                       newton_steps=newton_steps, split_digits=split_digits)
+                       newton_steps=newton_steps, split_digits=split_digits, use_graph=use_graph)
     n = len(pairs)
     da = [TTDesc(A) for A, _ in pairs]
     db = [TTDesc(B) for _, B in pairs]
@@ -266,12 +266,12 @@ def ttm_multiply_batched(handle, pairs, eps=0.0, chi_max=0, chi_out=0, prec="fp6
 
 
 def ttm_multiply(handle, A, B, eps=0.0, chi_max=0, chi_out=0, prec="fp64", max_sweeps=0, profile=0,
-                 f32_passes=0, jacobi_kernel=0, newton_steps=0, split_digits=0):
+                 f32_passes=0, jacobi_kernel=0, newton_steps=0, split_digits=0, use_graph=0):
     """Omega = A o B through ttm_multiply. Returns (cores, report)."""
     lib = handle.lib
     handle.set_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out, max_sweeps=max_sweeps,
                        profile=profile, f32_passes=f32_passes, jacobi_kernel=jacobi_kernel,
-                       newton_steps=newton_steps, split_digits=split_digits)
+                       newton_steps=newton_steps, split_digits=split_digits, use_graph=use_graph)
     a, b = TTDesc(A), TTDesc(B)
     o = make_options(prec=prec, eps=eps, chi_max=chi_max, chi_out=chi_out)
     cap = int(lib.ttm_output_capacity(ctypes.byref(a.c), ctypes.byref(b.c), ctypes.byref(o)))

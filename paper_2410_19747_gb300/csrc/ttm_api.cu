@@ -35,12 +35,88 @@ static ttm_status set_err(ttm_status s, const std::string& msg) {
 
 void Engine::load_core(const ttm_tt* T, int k, int buf) {
   if (!launch_) return;
+  if (defer_loads_) {  // a captured walk: the copies of every call are issued before the replay
+    hs_.graph_loads.push_back(T == A_ ? 0 : 1);
+    hs_.graph_loads.push_back(k);
+    hs_.graph_loads.push_back(buf);
+    return;
+  }
+  issue_load(T, k, buf, hs_.stream);
+}
+
+void Engine::issue_load(const ttm_tt* T, int k, int buf, cudaStream_t st) {
   for (int z = 0; z < Z_; ++z) {
     const ttm_tt& t = T[z];
     const size_t n = (size_t)t.bonds[k] * t.d * t.bonds[k + 1];
     TTM_CUDA(cudaMemcpyAsync(hbuf_[(size_t)z * nb_ + buf], t.cores[k], n * sizeof(double),
-                             t.on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, hs_.stream));
+                             t.on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
   }
+}
+
+// Everything that decides the launch walk: the options, the batch shape, every input bond
+// and the arena (the captured kernels hold pointers into it).
+std::string Engine::plan_key(void* arena) const {
+  std::string k((const char*)&opt_, sizeof(opt_));
+  auto put = [&](long v) { k.append((const char*)&v, sizeof(v)); };
+  put(Z_);
+  put(L_);
+  put(d_);
+  put((long)(size_t)arena);
+  put((long)bytes_needed());
+  for (int z = 0; z < Z_; ++z)
+    for (int i = 0; i <= L_; ++i) {
+      put(A_[z].bonds[i]);
+      put(B_[z].bonds[i]);
+    }
+  return k;
+}
+
+// use_graph: the first call of a plan runs the launch walk under stream capture (on a private
+// stream of the handle; the input copies are recorded instead) and instantiates the graph;
+// every call then issues its input copies on st and replays the graph there.
+void Engine::launch_walk_graph(void* arena, cudaStream_t st, int nchain_planned, int jac_planned) {
+  const std::string key = plan_key(arena);
+  if (hs_.graph_exec == nullptr || hs_.graph_key != key) {
+    if (hs_.graph_exec) {
+      TTM_CUDA(cudaGraphExecDestroy(hs_.graph_exec));
+      hs_.graph_exec = nullptr;
+    }
+    hs_.graph_key.clear();
+    hs_.graph_loads.clear();
+    if (!hs_.capture_stream) TTM_CUDA(cudaStreamCreateWithFlags(&hs_.capture_stream, cudaStreamNonBlocking));
+    const cudaStream_t saved = hs_.stream;
+    hs_.stream = hs_.capture_stream;
+    defer_loads_ = true;
+    cudaGraph_t g = nullptr;
+    reset_ids();
+    TTM_CUDA(cudaStreamBeginCapture(hs_.capture_stream, cudaStreamCaptureModeRelaxed));
+    try {
+      run();
+      if ((int)nbuf_total_ != nchain_planned || jac_launch_ != jac_planned)
+        throw Error(TTM_ERR_INVALID_ARG, "internal: plan and launch walks disagree");
+    } catch (...) {
+      cudaStreamEndCapture(hs_.capture_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      hs_.stream = saved;
+      defer_loads_ = false;
+      throw;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(hs_.capture_stream, &g);
+    hs_.stream = saved;
+    defer_loads_ = false;
+    TTM_CUDA(ec);
+    const cudaError_t ei = cudaGraphInstantiate(&hs_.graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    TTM_CUDA(ei);
+    hs_.graph_key = key;
+    hs_.graph_launches = launches_;
+    hs_.graph_gemms = (long)gemm_log_.size();
+  }
+  launches_ = hs_.graph_launches;
+  gemm_launch_count_ = hs_.graph_gemms;
+  for (size_t q = 0; q + 2 < hs_.graph_loads.size(); q += 3)
+    issue_load(hs_.graph_loads[q] == 0 ? A_ : B_, hs_.graph_loads[q + 1], hs_.graph_loads[q + 2], st);
+  TTM_CUDA(cudaGraphLaunch(hs_.graph_exec, st));
 }
 
 // Gauge move of one carriage (QR after Contract): C [bl][d][br] = Q R; C <- Q; Next <- R Next.
@@ -533,10 +609,14 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
   const int nchain_planned = nchain_;
   const int jac_planned = jac_launch_;
   launch_ = true;
-  reset_ids();
-  run();
-  if ((int)nbuf_total_ != nchain_planned || jac_launch_ != jac_planned)
-    throw Error(TTM_ERR_INVALID_ARG, "internal: plan and launch walks disagree");
+  if (graph_ok_ && opt_.use_graph) {
+    launch_walk_graph(arena, st, nchain_planned, jac_planned);
+  } else {
+    reset_ids();
+    run();
+    if ((int)nbuf_total_ != nchain_planned || jac_launch_ != jac_planned)
+      throw Error(TTM_ERR_INVALID_ARG, "internal: plan and launch walks disagree");
+  }
   if (hs_.ev1) TTM_CUDA(cudaEventRecord(hs_.ev1, st));
 
   // results
@@ -630,7 +710,7 @@ void Engine::execute(void* arena, const ttm_options& opt, std::vector<ttm_report
     r.jacobi64_ms = kind_ms[3];
     r.jacobi32_flops = stat[(size_t)0 * ns + ST_JFLOPS32];
     r.jacobi32_sweeps = (int64_t)stat[(size_t)z * ns + ST_JSWEEPS32];
-    r.gemm_launches = (int64_t)gemm_log_.size();
+    r.gemm_launches = gemm_launch_count_ >= 0 ? (int64_t)gemm_launch_count_ : (int64_t)gemm_log_.size();
     double gf = 0.0;  // counted on the device per executed problem; launch-wide like the others
     for (int zz = 0; zz < Z_; ++zz) gf += stat[(size_t)zz * ns + ST_GFLOPS];
     r.gemm_flops = gf;
@@ -700,8 +780,10 @@ static ttm_status check_opts(const ttm_options& o) {
   if (o.chi_max < 0 || o.chi_out < 0) return set_err(TTM_ERR_INVALID_ARG, "negative cap");
   if (o.prec != TTM_PREC_FP64 && o.prec != TTM_PREC_BF16_SPLIT)
     return set_err(TTM_ERR_INVALID_ARG, "unknown precision mode");
-  if (o.use_graph != 0 || o.check_finite != 0)
-    return set_err(TTM_ERR_UNSUPPORTED, "use_graph and check_finite are not built (must be 0)");
+  if (o.use_graph != 0 && o.use_graph != 1) return set_err(TTM_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+  if (o.use_graph && o.profile_kernels)
+    return set_err(TTM_ERR_UNSUPPORTED, "use_graph = 1 cannot be combined with profile_kernels = 1");
+  if (o.check_finite != 0) return set_err(TTM_ERR_UNSUPPORTED, "check_finite is not built (must be 0)");
   if (o.f32_passes < 0 || o.f32_passes > kMaxF32Passes)
     return set_err(TTM_ERR_INVALID_ARG, "f32_passes must lie in [0, 8]");
   if (o.jacobi_kernel != 0 && o.jacobi_kernel != 1 && o.jacobi_kernel != 2 && o.jacobi_kernel != 3 &&
@@ -740,6 +822,7 @@ static ttm_status multiply_impl(ttm_handle* h, int32_t n, const ttm_tt* A, const
   try {
     TTM_CUDA(cudaSetDevice(h->s.device));
     Engine e(h->s, n, A, B);
+    e.allow_graph();  // the handle's arena persists across calls
     e.plan();
     h->s.arena.ensure(e.bytes_needed());
     std::vector<ttm_report> reps(n);

@@ -49,6 +49,8 @@ class Engine {
   }
 
   size_t bytes_needed() const { return per_product_bytes() * Z_ + table_bytes() + (size_t)tc_bytes_ + 256; }
+  // use_graph may capture and replay this plan: only for an arena that persists across calls
+  void allow_graph() { graph_ok_ = true; }
 
   // ------------------------------------------------------------------ execution
   void execute(void* arena, const ttm_options& opt, std::vector<ttm_report>* reps, ttm_tt* outs);
@@ -355,6 +357,13 @@ class Engine {
 
   // ------------------------------------------------------------------ steps
   void load_core(const ttm_tt* T, int k, int buf);
+  void issue_load(const ttm_tt* T, int k, int buf, cudaStream_t st);
+  // use_graph: capture the launch walk once per plan, replay it afterwards
+  bool graph_ok_ = false;            // set by the caller whose arena persists across calls
+  bool defer_loads_ = false;         // capture: input copies are recorded, not captured
+  long gemm_launch_count_ = -1;      // replay: the GEMM count of the captured walk
+  std::string plan_key(void* arena) const;
+  void launch_walk_graph(void* arena, cudaStream_t st, int nchain_planned, int jac_planned);
   void qr_move(int c, int& nx, int bl, int& br, int brr);
   int swap(int x, int y, int bl, int bm, int br, int kind = SK_SWAP);
   void jacobi32(int pass, int slot, Dim m, Dim n, int m_ub, int n_ub, int npad_ub, long pairs, int sweeps);

@@ -71,8 +71,17 @@ struct HandleState {
   DeviceArena env_arena;  // environments of ttm_inner / ttm_inner3 / ttm_backward
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> prof_events;  // pairs around Jacobi launches (profile_kernels)
+  // use_graph = 1: the launch walk of the last plan, captured once into a CUDA graph and
+  // replayed while the plan (options, shapes, input bonds, arena) stays the same
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::string graph_key;
+  std::vector<int> graph_loads;          // (input: 0 = A, 1 = B; core k; buffer) per input copy
+  long graph_launches = 0, graph_gemms = 0;
   ~HandleState() {
     for (cudaEvent_t e : prof_events) cudaEventDestroy(e);
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
 

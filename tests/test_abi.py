@@ -66,12 +66,13 @@ def test_option_validation_without_gpu(lib):
     import paper_2410_19747_gb300.binding as b
     h = ctypes.c_void_p()
     for kw, status in ((dict(jacobi_kernel=5), -1), (dict(f32_passes=9), -1), (dict(f32_passes=-1), -1),
-                       (dict(newton_steps=9), -1), (dict(newton_steps=-1), -1), (dict(use_graph=1), -9)):
+                       (dict(newton_steps=9), -1), (dict(newton_steps=-1), -1), (dict(use_graph=2), -1),
+                       (dict(use_graph=1, profile=1), -9)):
         o = b.make_options(**kw)
         assert lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == status, kw
     # accepted options get past validation: without a GPU the next step is a CUDA error
     for kw in (dict(jacobi_kernel=8), dict(jacobi_kernel=16), dict(f32_passes=1), dict(chi_max=16, chi_out=8),
-               dict(chi_max=0, chi_out=8), dict(newton_steps=1, chi_max=16)):
+               dict(chi_max=0, chi_out=8), dict(newton_steps=1, chi_max=16), dict(use_graph=1)):
         o = b.make_options(**kw)
         st = lib.ttm_create(ctypes.byref(h), 0, None, ctypes.byref(o))
         assert st not in (-1, -9), (kw, st, lib.ttm_last_error())
